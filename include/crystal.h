@@ -1,0 +1,224 @@
+/* crystal.h — C ABI of the GB300 (sm_103a) tile-based query operators.
+ *
+ * The operators follow the statements of the problems in "A Study of the Fundamental
+ * Performance Characteristics of GPUs and CPUs for Database Analytics" (Shanbhag,
+ * Madden, Yu; SIGMOD 2020), Section 3 (tile-based execution model), Section 4
+ * (project, select, hash join, sort) and Section 5.3 (fused select-join-aggregate
+ * query kernels).
+ *
+ * Conventions shared by every call
+ *  - All column pointers are caller-owned DEVICE memory on the current device; the
+ *    library never frees them.  Column pointers must be 16-byte aligned (the kernels
+ *    move whole 16-byte vectors); a misaligned pointer returns CRYS_EINVAL.
+ *  - Every call is asynchronous on the given stream (NULL = legacy default stream).
+ *    Outputs in device memory are valid once that stream is synchronised.
+ *  - Return value: CRYS_OK or a negative CRYS_E* status detected on the host before
+ *    anything was launched (nothing was enqueued in that case).
+ *  - Conditions only the GPU can see (a wait that exceeded its time bound, a full
+ *    hash table, a reserved or duplicate key, a group code out of range) set sticky
+ *    bits in a per-device error word read with crys_device_errors(); the kernels
+ *    never trap, and a kernel that detects one of these stops its own work early.
+ *  - n == 0 is legal everywhere and produces empty / zero results.
+ *  - Scratch: calls that need scratch take (void* d_temp, size_t* temp_bytes).  With
+ *    d_temp == NULL the call only stores the required size in *temp_bytes and returns
+ *    CRYS_OK; otherwise *temp_bytes must be at least that size (else CRYS_ENOMEM).
+ *    Scratch is caller-owned device memory, 256-byte aligned, used only while the call's
+ *    work runs on its stream.
+ */
+#ifndef CRYSTAL_H
+#define CRYSTAL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* crys_stream; /* the same type as cudaStream_t */
+
+/* ------------------------------------------------------------------ status */
+#define CRYS_OK 0
+#define CRYS_EINVAL (-1)   /* bad argument: null/misaligned pointer, bad size, bad plan */
+#define CRYS_ENOMEM (-2)   /* scratch smaller than required */
+#define CRYS_EFULL (-3)    /* hash table capacity too small for the rows to insert */
+#define CRYS_ETIMEOUT (-4) /* reserved for host waits that exceeded their bound */
+#define CRYS_ECUDA (-5)    /* a CUDA runtime call failed (launch or memset) */
+
+/* Bits of the per-device error word (crys_device_errors). */
+#define CRYS_DEV_TIMEOUT 0x1    /* a bounded spin-wait (mbarrier, look-back) gave up */
+#define CRYS_DEV_TABLE_FULL 0x2 /* an insert probed the whole table without a free slot */
+#define CRYS_DEV_BAD_KEY 0x4    /* key -1 (0xFFFFFFFF, the empty-slot marker) on build */
+#define CRYS_DEV_DUP_KEY 0x8    /* a build key was inserted twice */
+#define CRYS_DEV_BAD_GROUP 0x10 /* a joined group code was outside [0, group_card) */
+#define CRYS_DEV_BOUNDS 0x20    /* an output position fell outside its buffer (skipped) */
+
+/* Human-readable text for a status code. */
+const char* crys_strerror(int status);
+
+/* Copies the calling device's error word into *flags after synchronising `s`; when
+ * `clear` is non-zero the word is reset to 0 (also ordered on `s`). */
+int crys_device_errors(int32_t* flags, int clear, crys_stream s);
+
+/* Total number of kernels this library has launched in this process (all devices). */
+int64_t crys_launch_count(void);
+
+/* ------------------------------------------------------------------ selection
+ * Section 3.2 (query Q0, Figure "tile-example") and Section 4.2 (query Q3):
+ * SELECT x FROM R WHERE lo <= x <= hi, as one kernel: each thread block loads a tile,
+ * evaluates the predicate, computes per-thread offsets with a block-wide scan, reserves
+ * its output range once per tile and writes the compacted tile with coalesced stores.
+ * The inclusive range expresses "<", "<=", "==", ">" and BETWEEN on int32.
+ *   x          n int32 values (device)
+ *   out        capacity for n int32 values (device); receives the selected values
+ *   d_count    one int64 (device); receives the number of selected values
+ *   order_preserving
+ *              0: the paper's scheme, one atomic reservation per tile — tiles land in
+ *                 completion order, values inside a tile keep input order.  No scratch.
+ *              1: tiles are chained by a decoupled look-back scan so that `out` is in
+ *                 input order.  Needs scratch (see conventions).
+ */
+int crys_select(const int32_t* x, int64_t n, int32_t lo, int32_t hi, int32_t* out,
+                int64_t* d_count, int order_preserving, void* d_temp, size_t* temp_bytes,
+                crys_stream s);
+
+/* ------------------------------------------------------------------ projection
+ * Section 4.1, queries Q1 and Q2: y = a*x1 + b*x2 (CRYS_PROJ_LINEAR) or the sigmoid
+ * 1/(1 + exp(-(a*x1 + b*x2))) (CRYS_PROJ_SIGMOID), float32 in and out, one rounding per
+ * multiply and per add (no fused multiply-add), IEEE division and expf.
+ *   x1, x2, y  n float32 values each (device); y may alias x1 or x2. */
+#define CRYS_PROJ_LINEAR 0
+#define CRYS_PROJ_SIGMOID 1
+int crys_project(const float* x1, const float* x2, int64_t n, float a, float b, int op, float* y,
+                 crys_stream s);
+
+/* ------------------------------------------------------------------ hash join
+ * Section 4.3: no-partitioning hash join over a linear-probing table that is a plain
+ * array of 8-byte slots (no pointers).  Slot = key in the low 32 bits, value in the high
+ * 32 bits; an empty slot is all ones, so key -1 cannot be stored.  Slot of key k:
+ * multiplicative (Fibonacci) hashing, (uint32)(k * 2654435769) >> (32 - log2(capacity)),
+ * then linear probing with wrap-around.  capacity is a power of two; the paper's tables
+ * run at 50% fill, i.e. capacity = 2 * rows. */
+typedef struct {
+  uint64_t* slots;  /* capacity slots (device), caller-owned */
+  int64_t capacity; /* power of two, >= 2 */
+} crys_hash;
+
+/* Conjunctive range predicate on a device column: lo <= col[row] <= hi. */
+typedef struct {
+  const int32_t* col;
+  int32_t lo, hi;
+} crys_pred;
+
+/* Marks every slot empty.  Must precede the first build into a table. */
+int crys_hash_init(const crys_hash* ht, crys_stream s);
+
+/* Build phase: inserts (keys[i], vals[i]) for every row i passing all `n_filters`
+ * predicates (the dimension filter of a select-join query is applied at build time,
+ * Section 5.3).  vals may be NULL (value 0, membership only).  Keys must be unique and
+ * != -1.  Without filters the capacity must exceed n (CRYS_EFULL otherwise). */
+int crys_hash_build(const int32_t* keys, const int32_t* vals, int64_t n,
+                    const crys_pred* filters, int32_t n_filters, const crys_hash* ht,
+                    crys_stream s);
+
+/* Probe phase fused with aggregation (Section 4.3, query Q4 with SUM(payload * value)):
+ * for each probe row whose key is in the table, sum += (int64)payload[i] * value.
+ * Per-thread sums are reduced per thread block and added to *d_sum with one atomic per
+ * block.  Sums wrap modulo 2^64.
+ *   d_sum      one int64 (device), overwritten
+ *   d_matches  one int64 (device) counting matching probe rows, or NULL */
+int crys_probe_aggregate(const int32_t* fk, const int32_t* payload, int64_t n,
+                         const crys_hash* ht, int64_t* d_sum, int64_t* d_matches,
+                         crys_stream s);
+
+/* ------------------------------------------------------------------ sort
+ * Section 4.4: least-significant-digit radix sort of (key, value) pairs by signed int32
+ * key, 8-bit digits, 4 passes, stable.  One up-front pass histograms all four digits;
+ * each digit pass ranks a tile stably inside the thread block and finds the tile's
+ * output offsets with a chained (decoupled look-back) scan.  n <= 2^30 - 1.
+ * keys_out/vals_out must not overlap the inputs; the inputs are not modified. */
+int crys_sort(const int32_t* keys_in, const int32_t* vals_in, int32_t* keys_out,
+              int32_t* vals_out, int64_t n, void* d_temp, size_t* temp_bytes, crys_stream s);
+
+/* ------------------------------------------------------------------ query plans
+ * Section 5.3: a select-join-aggregate query runs as one build kernel per dimension
+ * (crys_hash_build with the dimension's filter) and ONE probe kernel over the fact
+ * table that, per tile, applies the fact predicates, probes the dimension tables in
+ * plan order (rows that miss are dropped), forms the group id from the joined values,
+ * and accumulates SUM(expr) and COUNT per group.  Group id g is the mixed-radix number
+ * of the grouped joins' values (first grouped join most significant); the number of
+ * groups G is the product of their group_card (1 when nothing is grouped). */
+#define CRYS_MAX_COLS 16
+#define CRYS_MAX_PREDS 8
+#define CRYS_MAX_JOINS 4
+#define CRYS_MAX_PLANS 32
+
+#define CRYS_AGG_A 0       /* SUM(a) */
+#define CRYS_AGG_A_MUL_B 1 /* SUM(a * b) */
+#define CRYS_AGG_A_SUB_B 2 /* SUM(a - b) */
+#define CRYS_AGG_A_ADD_B 3 /* SUM(a + b) */
+
+typedef struct {
+  const int32_t* cols[CRYS_MAX_COLS]; /* device columns, n_rows values each */
+  int32_t n_cols;
+  int64_t n_rows;
+} crys_table;
+
+typedef struct {
+  int32_t col; /* fact column index */
+  int32_t lo, hi;
+} crys_col_pred;
+
+typedef struct {
+  int32_t fk_col;     /* fact column holding the foreign key */
+  crys_hash ht;       /* filtered dimension table: key -> group value */
+  int32_t group_card; /* 0: membership only; else the value is a group code in [0, card) */
+} crys_join;
+
+typedef struct {
+  int32_t n_preds;
+  crys_col_pred preds[CRYS_MAX_PREDS];
+  int32_t n_joins;
+  crys_join joins[CRYS_MAX_JOINS];
+  int32_t agg_op, agg_a, agg_b; /* CRYS_AGG_*, fact column indices */
+  int64_t* d_sums;              /* G int64 (device) */
+  int64_t* d_counts;            /* G int64 (device) or NULL */
+} crys_plan;
+
+/* Number of groups G of a plan (product of group_card over grouped joins). */
+int crys_plan_groups(const crys_plan* plan, int64_t* groups);
+
+/* One query over all fact rows; overwrites the plan's outputs. */
+int crys_run_plan(const crys_table* fact, const crys_plan* plan, crys_stream s);
+
+/* Shared scan: up to CRYS_MAX_PLANS queries over rows [row_begin, row_end) of the same
+ * fact table in ONE kernel: each tile of the union of the queries' columns is read from
+ * HBM once (staged in shared memory by bulk asynchronous copies) and every query is
+ * evaluated on it.  With CRYS_ACCUMULATE the outputs are added to instead of
+ * overwritten, so a query can be carried across several row segments (a circular
+ * scan that queries join and leave at segment boundaries).  row_begin must be a
+ * multiple of 4. */
+#define CRYS_ACCUMULATE 0x1
+int crys_run_plans(const crys_table* fact, const crys_plan* plans, int32_t n_plans,
+                   int64_t row_begin, int64_t row_end, int flags, crys_stream s);
+
+/* ------------------------------------------------------------------ tile shapes
+ * Each operator is compiled for several tile shapes (threads per block x items per
+ * thread, Section 3.3).  crys_tile_variants lists them; crys_set_tile picks the one
+ * used by later calls in this process (an autotuner sweeps and persists the choice). */
+#define CRYS_OP_SELECT 0
+#define CRYS_OP_PROJECT 1
+#define CRYS_OP_PROBE 2
+#define CRYS_OP_PLAN 3
+#define CRYS_OP_SHARED_SCAN 4
+#define CRYS_OP_SORT 5
+#define CRYS_NUM_OPS 6
+/* Writes up to `max` (threads, items) pairs; returns the number of variants (or <0). */
+int crys_tile_variants(int op, int32_t* threads, int32_t* items, int32_t max);
+int crys_set_tile(int op, int32_t variant);
+int crys_get_tile(int op);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CRYSTAL_H */

@@ -1,0 +1,114 @@
+// Host-side state of the library: the per-device sticky error word, the launch
+// counter, SM counts and the tile-shape choice of each operator.
+#include <atomic>
+#include <mutex>
+
+#include "common.cuh"
+#include "tiles.h"
+
+namespace crys {
+namespace {
+
+// Sticky error bits set by kernels (CRYS_DEV_*).  One copy per device that loads the
+// library; kernels receive its address as an argument.
+__device__ int32_t g_device_error = 0;
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mutex;
+int32_t* g_error_ptr[kMaxDevices] = {};
+int g_sms[kMaxDevices] = {};
+std::atomic<int64_t> g_launches{0};
+std::atomic<int> g_variant[CRYS_NUM_OPS] = {};
+
+int current_device() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return 0;
+  return dev;
+}
+
+}  // namespace
+
+int32_t* device_error_word() {
+  const int dev = current_device();
+  std::lock_guard<std::mutex> lock(g_mutex);
+  if (!g_error_ptr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_device_error) != cudaSuccess) return nullptr;
+    g_error_ptr[dev] = static_cast<int32_t*>(p);
+  }
+  return g_error_ptr[dev];
+}
+
+void note_launch(int kernels) { g_launches.fetch_add(kernels, std::memory_order_relaxed); }
+
+int sm_count() {
+  const int dev = current_device();
+  std::lock_guard<std::mutex> lock(g_mutex);
+  if (!g_sms[dev]) {
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    g_sms[dev] = v > 0 ? v : 1;
+  }
+  return g_sms[dev];
+}
+
+int tile_variant(int op) {
+  if (op < 0 || op >= CRYS_NUM_OPS) return 0;
+  return g_variant[op].load(std::memory_order_relaxed);
+}
+
+}  // namespace crys
+
+extern "C" {
+
+const char* crys_strerror(int status) {
+  switch (status) {
+    case CRYS_OK: return "ok";
+    case CRYS_EINVAL: return "invalid argument (null, misaligned or out-of-range value, bad plan)";
+    case CRYS_ENOMEM: return "scratch buffer smaller than required";
+    case CRYS_EFULL: return "hash table capacity too small";
+    case CRYS_ETIMEOUT: return "wait exceeded its bound";
+    case CRYS_ECUDA: return "CUDA runtime error";
+    default: return "unknown status";
+  }
+}
+
+int crys_device_errors(int32_t* flags, int clear, crys_stream s) {
+  if (!flags) return CRYS_EINVAL;
+  int32_t* word = crys::device_error_word();
+  if (!word) return CRYS_ECUDA;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(s);
+  int32_t host = 0;
+  if (cudaMemcpyAsync(&host, word, sizeof(int32_t), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return CRYS_ECUDA;
+  if (clear && cudaMemsetAsync(word, 0, sizeof(int32_t), st) != cudaSuccess) return CRYS_ECUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return CRYS_ECUDA;
+  *flags = host;
+  return CRYS_OK;
+}
+
+int64_t crys_launch_count(void) { return crys::g_launches.load(); }
+
+int crys_tile_variants(int op, int32_t* threads, int32_t* items, int32_t max) {
+  if (op < 0 || op >= CRYS_NUM_OPS) return CRYS_EINVAL;
+  const int n = crys::kNumVariants[op];
+  for (int i = 0; i < n && i < max; ++i) {
+    if (threads) threads[i] = crys::kTiles[op][i].threads;
+    if (items) items[i] = crys::kTiles[op][i].items;
+  }
+  return n;
+}
+
+int crys_set_tile(int op, int32_t variant) {
+  if (op < 0 || op >= CRYS_NUM_OPS || variant < 0 || variant >= crys::kNumVariants[op])
+    return CRYS_EINVAL;
+  crys::g_variant[op].store(variant);
+  return CRYS_OK;
+}
+
+int crys_get_tile(int op) {
+  if (op < 0 || op >= CRYS_NUM_OPS) return CRYS_EINVAL;
+  return crys::g_variant[op].load();
+}
+
+}  // extern "C"

@@ -1,0 +1,236 @@
+// Device building blocks shared by the operator kernels: bulk asynchronous copies
+// (TMA, cp.async.bulk) into shared memory with mbarrier completion, bounded waits,
+// warp/block scans and reductions, and the hash function.  These are the sm_103a
+// counterparts of the paper's block-wide functions (Section 3.3, Table "list-func"):
+// BlockLoad = bulk copy of a tile into a shared-memory stage; BlockPred / BlockScan /
+// BlockShuffle / BlockStore / BlockLookup / BlockAggregate are written out in each
+// kernel on top of the helpers below.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "crystal.h"
+#include "internal.h"
+
+namespace crys {
+
+constexpr int kWarp = 32;
+// Upper bound of any spin-wait, in nanoseconds of %globaltimer.  Legitimate waits are
+// microseconds; after this bound the waiting thread sets CRYS_DEV_TIMEOUT and its block
+// abandons the work instead of hanging the GPU.
+constexpr uint64_t kWaitBoundNs = 2000000000ull;
+constexpr uint64_t kEmptySlot = 0xFFFFFFFFFFFFFFFFull;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint64_t global_timer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void set_error(int32_t* err, int32_t bits) {
+  atomicOr(reinterpret_cast<int*>(err), bits);
+}
+
+__device__ __forceinline__ int32_t read_error(const int32_t* err) {
+  return *reinterpret_cast<const volatile int32_t*>(err);
+}
+
+// ---------------------------------------------------------------- mbarrier + TMA
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+
+// Makes barrier initialisation visible to the async (TMA) proxy.
+__device__ __forceinline__ void fence_barrier_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// Orders this thread's generic-proxy shared-memory accesses before later async-proxy
+// accesses (a stage that was read by threads is about to be overwritten by TMA).
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar_addr, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(done)
+      : "r"(bar_addr), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+// Waits for phase `parity` of the barrier to complete, at most kWaitBoundNs.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int32_t* err) {
+  const uint32_t addr = smem_u32(bar);
+  if (mbar_try_wait(addr, parity)) return true;
+  const uint64_t t0 = global_timer_ns();
+  while (true) {
+    if (mbar_try_wait(addr, parity)) return true;
+    if (global_timer_ns() - t0 > kWaitBoundNs) {
+      set_error(err, CRYS_DEV_TIMEOUT);
+      return false;
+    }
+  }
+}
+
+// L2 eviction policies for bulk copies and loads: streamed columns are read once
+// (evict_first) so that hash tables probed at random stay resident (evict_last).
+__device__ __forceinline__ uint64_t policy_evict_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t policy_evict_last() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+
+// One-dimensional bulk copy global -> shared (TMA engine), completing `bytes` of
+// transaction count on `bar`.  src and dst 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_load(void* dst_smem, const void* src, uint32_t bytes,
+                                          uint64_t* bar, uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint "
+      "[%0], [%1], %2, [%3], %4;" ::"r"(smem_u32(dst_smem)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(policy)
+      : "memory");
+}
+
+// ---------------------------------------------------------------- global loads
+
+// Streaming column loads: not allocated in L1, L2 policy from policy_evict_first().
+__device__ __forceinline__ int4 ld_stream_v4(const int32_t* p, uint64_t pol) {
+  int4 v;
+  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.s32 {%0,%1,%2,%3}, [%4], %5;"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "l"(p), "l"(pol));
+  return v;
+}
+
+__device__ __forceinline__ int32_t ld_stream(const int32_t* p, uint64_t pol) {
+  int32_t v;
+  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.s32 %0, [%1], %2;"
+               : "=r"(v)
+               : "l"(p), "l"(pol));
+  return v;
+}
+
+// Hash-table slot read with the L2 policy from policy_evict_last() (tables are read-only
+// while they are probed and should outlive the streamed columns in L2).
+__device__ __forceinline__ uint64_t ld_slot(const uint64_t* p, uint64_t pol) {
+  uint64_t v;
+  asm volatile("ld.global.nc.L2::cache_hint.u64 %0, [%1], %2;" : "=l"(v) : "l"(p), "l"(pol));
+  return v;
+}
+
+__device__ __forceinline__ uint64_t ld_relaxed_u64(const uint64_t* p) {
+  uint64_t v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed_u64(uint64_t* p, uint64_t v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed_u32(uint32_t* p, uint32_t v) {
+  asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// ---------------------------------------------------------------- hashing
+
+// Fibonacci (multiplicative) hashing: the top log2(capacity) bits of k * 2^32/phi.
+__device__ __forceinline__ uint32_t hash_slot(int32_t key, uint32_t shift) {
+  return static_cast<uint32_t>(
+      (static_cast<uint64_t>(static_cast<uint32_t>(key) * 2654435769u)) >> shift);
+}
+
+// Looks `key` up by linear probing; returns the value, or false when absent.
+__device__ __forceinline__ bool hash_find(const uint64_t* slots, uint32_t mask, uint32_t shift,
+                                          int32_t key, int32_t* value, uint64_t pol) {
+  uint32_t h = hash_slot(key, shift);
+  for (uint32_t probe = 0; probe <= mask; ++probe) {
+    uint64_t s = ld_slot(slots + h, pol);
+    if (s == kEmptySlot) return false;
+    if (static_cast<uint32_t>(s) == static_cast<uint32_t>(key)) {
+      *value = static_cast<int32_t>(s >> 32);
+      return true;
+    }
+    h = (h + 1) & mask;
+  }
+  return false;
+}
+
+// Continues a probe whose first slot `s` (at index h) was already loaded.
+__device__ __forceinline__ bool hash_resolve(const uint64_t* slots, uint32_t mask, uint32_t h,
+                                             uint64_t s, int32_t key, int32_t* value,
+                                             uint64_t pol) {
+  for (uint32_t probe = 0; probe <= mask; ++probe) {
+    if (s == kEmptySlot) return false;
+    if (static_cast<uint32_t>(s) == static_cast<uint32_t>(key)) {
+      *value = static_cast<int32_t>(s >> 32);
+      return true;
+    }
+    h = (h + 1) & mask;
+    s = ld_slot(slots + h, pol);
+  }
+  return false;
+}
+
+// ---------------------------------------------------------------- scans / reductions
+
+__device__ __forceinline__ int32_t warp_inclusive_scan(int32_t v, int lane) {
+#pragma unroll
+  for (int d = 1; d < kWarp; d <<= 1) {
+    int32_t u = __shfl_up_sync(0xFFFFFFFFu, v, d);
+    if (lane >= d) v += u;
+  }
+  return v;
+}
+
+__device__ __forceinline__ uint64_t warp_sum_u64(uint64_t v) {
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, d);
+  return v;
+}
+
+// Block-wide sum of one uint64 per thread; result valid in thread 0.
+// `scratch` holds one uint64 per warp.
+template <int THREADS>
+__device__ __forceinline__ uint64_t block_sum_u64(uint64_t v, uint64_t* scratch) {
+  constexpr int WARPS = THREADS / kWarp;
+  const int lane = threadIdx.x % kWarp, warp = threadIdx.x / kWarp;
+  v = warp_sum_u64(v);
+  if (lane == 0) scratch[warp] = v;
+  __syncthreads();
+  uint64_t total = 0;
+  if (warp == 0) {
+    uint64_t w = lane < WARPS ? scratch[lane] : 0ull;
+    total = warp_sum_u64(w);
+  }
+  __syncthreads();
+  return total;
+}
+
+}  // namespace crys

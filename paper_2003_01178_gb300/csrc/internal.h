@@ -1,0 +1,57 @@
+// Host-side internals shared by the operator translation units (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "crystal.h"
+
+namespace crys {
+
+// Device pointer of the calling device's sticky error word (see crys_device_errors).
+int32_t* device_error_word();
+
+// Counts one kernel launch of this library.
+void note_launch(int kernels = 1);
+
+// Number of SMs of the current device.
+int sm_count();
+
+// Current tile variant of an operator (index into its variant table).
+int tile_variant(int op);
+
+inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+inline int check_launch() { return cudaGetLastError() == cudaSuccess ? CRYS_OK : CRYS_ECUDA; }
+
+inline uint32_t log2_pow2(uint64_t v) {
+  uint32_t r = 0;
+  while ((1ull << r) < v) ++r;
+  return r;
+}
+
+inline bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
+
+// Persistent grid: resident blocks per SM (from the occupancy calculator) x SMs,
+// capped by the number of tiles.
+template <typename K>
+int persistent_grid(K kernel, int threads, size_t smem, int64_t tiles) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) !=
+          cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  int64_t g = static_cast<int64_t>(per_sm) * sm_count();
+  if (tiles < g) g = tiles;
+  return g < 1 ? 1 : static_cast<int>(g);
+}
+
+// Opts a kernel into more than 48 KB of dynamic shared memory (once per process).
+template <typename K>
+bool allow_smem(K kernel, size_t bytes) {
+  if (bytes <= 48 * 1024) return true;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              static_cast<int>(bytes)) == cudaSuccess;
+}
+
+}  // namespace crys

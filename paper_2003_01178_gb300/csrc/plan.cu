@@ -1,0 +1,627 @@
+// Fused select-join-aggregate pipelines (Section 5.3; Figure "tile-extension"): after
+// one build kernel per dimension, ONE kernel streams the fact table in tiles and, per
+// tile, applies the fact predicates (BlockPred), loads later columns only for rows still
+// alive (BlockLoadSel: a 16-byte group is fetched only if one of its rows is alive), probes
+// the dimension tables in plan order (BlockLookup), forms the group id from the joined
+// values and accumulates SUM(expr) and COUNT per group (BlockAggregate into per-block
+// partials, flushed with one atomic per non-empty group and block).
+//
+// Two kernels share the per-query evaluation:
+//  * plan_kernel       one query; columns read straight from global memory so that
+//                      BlockLoadSel saves sectors of dead rows.
+//  * shared_scan_kernel up to 32 queries over the same fact table; the union of their
+//                      columns is staged per tile in shared memory by bulk copies, so each
+//                      fact tile crosses HBM once however many queries read it.
+#include "common.cuh"
+#include "pipeline.cuh"
+#include "tiles.h"
+
+namespace crys {
+namespace {
+
+enum AccMode : int32_t { kAccSingle = 0, kAccShared = 1, kAccGlobal = 2 };
+
+struct DevJoin {
+  const uint64_t* slots;
+  uint32_t mask, shift;
+  int32_t fk_col;
+  int32_t card;  // 0: membership only
+};
+
+struct DevQuery {
+  int32_t n_preds;
+  int32_t pred_col[CRYS_MAX_PREDS];
+  int32_t pred_lo[CRYS_MAX_PREDS];
+  int32_t pred_hi[CRYS_MAX_PREDS];
+  int32_t n_joins;
+  DevJoin joins[CRYS_MAX_JOINS];
+  int32_t agg_op, agg_a, agg_b;
+  int32_t acc_mode;
+  int32_t acc_off;  // first shared-memory accumulator of this query
+  int64_t groups;
+  unsigned long long* sums;
+  unsigned long long* counts;
+};
+
+// Column access from global memory (plan_kernel).  Tiles start at multiples of 4 rows
+// from a 4-row-aligned segment start, so full groups are 16-byte vector loads.
+struct GlobalCols {
+  const int32_t* const* cols;
+  int64_t row0;
+  int valid;
+  uint64_t pol;
+  __device__ __forceinline__ int4 load4(int c, int p) const {
+    const int32_t* src = cols[c] + row0 + p;
+    if (p + 4 <= valid) return ld_stream_v4(src, pol);
+    int v[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) v[e] = p + e < valid ? ld_stream(src + e, pol) : 0;
+    return make_int4(v[0], v[1], v[2], v[3]);
+  }
+};
+
+// Column access from the shared-memory stage (shared_scan_kernel).
+struct StagedCols {
+  const int32_t* const* cols;
+  const int32_t* slot_of;  // table column -> staged slice
+  const int32_t* stage;
+  int tile;
+  int64_t row0;
+  int valid, bulk;
+  __device__ __forceinline__ int4 load4(int c, int p) const {
+    return stage_read4(stage + slot_of[c] * tile, cols[c] + row0, p, bulk, valid);
+  }
+};
+
+__device__ __forceinline__ void unpack4(int4 q, int32_t* dst) {
+  dst[0] = q.x;
+  dst[1] = q.y;
+  dst[2] = q.z;
+  dst[3] = q.w;
+}
+
+// Evaluates one query on this thread's ITEMS rows of a tile (4-row groups
+// j*THREADS + tid).  Returns the bitmap of rows that qualify; gid/val hold their group
+// id and aggregate value.
+template <int THREADS, int ITEMS, typename Cols>
+__device__ __forceinline__ uint32_t eval_query(const DevQuery& q, const Cols& cols, int valid,
+                                               int32_t (&gid)[ITEMS], int64_t (&val)[ITEMS],
+                                               int32_t* err, uint64_t pol_table) {
+  constexpr int VEC = ITEMS / 4;
+  const int tid = threadIdx.x;
+  uint32_t alive = 0;
+#pragma unroll
+  for (int j = 0; j < VEC; ++j) {
+    const int p = (j * THREADS + tid) * 4;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) alive |= static_cast<uint32_t>(p + e < valid) << (4 * j + e);
+  }
+  // BlockPred over the fact predicates, each column read only for live groups.
+  for (int f = 0; f < q.n_preds && alive; ++f) {
+    const int c = q.pred_col[f];
+    const int32_t lo = q.pred_lo[f], hi = q.pred_hi[f];
+#pragma unroll
+    for (int j = 0; j < VEC; ++j) {
+      if ((alive >> (4 * j)) & 0xFu) {
+        int32_t v[4];
+        unpack4(cols.load4(c, (j * THREADS + tid) * 4), v);
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+          if (v[e] < lo || v[e] > hi) alive &= ~(1u << (4 * j + e));
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < ITEMS; ++i) gid[i] = 0;
+  // BlockLookup into each dimension table, in plan order.
+  for (int jn = 0; jn < q.n_joins && alive; ++jn) {
+    const DevJoin& J = q.joins[jn];
+    int32_t key[ITEMS];
+#pragma unroll
+    for (int j = 0; j < VEC; ++j) {
+      if ((alive >> (4 * j)) & 0xFu)
+        unpack4(cols.load4(J.fk_col, (j * THREADS + tid) * 4), key + 4 * j);
+      else
+        key[4 * j] = key[4 * j + 1] = key[4 * j + 2] = key[4 * j + 3] = 0;
+    }
+    uint32_t h[ITEMS];
+    uint64_t slot[ITEMS];
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+      h[i] = hash_slot(key[i], J.shift);
+      slot[i] = ((alive >> i) & 1u) ? ld_slot(J.slots + h[i], pol_table) : kEmptySlot;
+    }
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+      if (!((alive >> i) & 1u)) continue;
+      int32_t value;
+      if (!hash_resolve(J.slots, J.mask, h[i], slot[i], key[i], &value, pol_table)) {
+        alive &= ~(1u << i);
+      } else if (J.card > 0) {
+        if (static_cast<uint32_t>(value) >= static_cast<uint32_t>(J.card)) {
+          set_error(err, CRYS_DEV_BAD_GROUP);
+          alive &= ~(1u << i);
+        } else {
+          gid[i] = gid[i] * J.card + value;
+        }
+      }
+    }
+  }
+  if (!alive) return 0;
+  // BlockLoadSel of the aggregate operands and the expression in int64.
+#pragma unroll
+  for (int j = 0; j < VEC; ++j) {
+    if (!((alive >> (4 * j)) & 0xFu)) continue;
+    const int p = (j * THREADS + tid) * 4;
+    int32_t va[4], vb[4] = {0, 0, 0, 0};
+    unpack4(cols.load4(q.agg_a, p), va);
+    if (q.agg_op != CRYS_AGG_A) unpack4(cols.load4(q.agg_b, p), vb);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int64_t x = va[e], y = vb[e];
+      int64_t r;
+      switch (q.agg_op) {
+        case CRYS_AGG_A_MUL_B: r = x * y; break;
+        case CRYS_AGG_A_SUB_B: r = x - y; break;
+        case CRYS_AGG_A_ADD_B: r = x + y; break;
+        default: r = x; break;
+      }
+      val[4 * j + e] = r;
+    }
+  }
+  return alive;
+}
+
+// Accumulator shared memory of a block: sums (8 B) then counts (4 B) per group.
+struct SharedAcc {
+  unsigned long long* sums;
+  unsigned int* counts;
+};
+
+__device__ __forceinline__ SharedAcc shared_acc(unsigned char* base, int groups) {
+  SharedAcc s;
+  s.sums = reinterpret_cast<unsigned long long*>(base);
+  s.counts = reinterpret_cast<unsigned int*>(base + static_cast<size_t>(groups) * 8);
+  return s;
+}
+
+template <int THREADS>
+__device__ __forceinline__ void flush_shared(const SharedAcc& acc, int first, int64_t groups,
+                                             unsigned long long* sums, unsigned long long* counts) {
+  for (int64_t g = threadIdx.x; g < groups; g += THREADS) {
+    const unsigned int c = acc.counts[first + g];
+    if (c) {
+      atomicAdd(sums + g, acc.sums[first + g]);
+      if (counts) atomicAdd(counts + g, static_cast<unsigned long long>(c));
+    }
+  }
+}
+
+// ------------------------------------------------------------------ one query
+
+struct PlanArgs {
+  const int32_t* cols[CRYS_MAX_COLS];
+  int64_t row_begin, row_end;
+  DevQuery q;
+  int32_t* err;
+};
+
+template <int THREADS, int ITEMS>
+__global__ void __launch_bounds__(THREADS) plan_kernel(const __grid_constant__ PlanArgs a) {
+  constexpr int TILE = THREADS * ITEMS;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ uint64_t red[THREADS / kWarp];
+  const DevQuery& q = a.q;
+  const int groups_sh = q.acc_mode == kAccShared ? static_cast<int>(q.groups) : 0;
+  const SharedAcc acc = shared_acc(smem_raw, groups_sh);
+  for (int g = threadIdx.x; g < groups_sh; g += THREADS) {
+    acc.sums[g] = 0;
+    acc.counts[g] = 0;
+  }
+  __syncthreads();
+
+  const int64_t nrows = a.row_end - a.row_begin;
+  const int64_t ntiles = (nrows + TILE - 1) / TILE;
+  uint64_t my_sum = 0, my_count = 0;
+  const uint64_t pol = policy_evict_first();
+  const uint64_t pol_table = policy_evict_last();
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    GlobalCols cols;
+    cols.pol = pol;
+    cols.cols = a.cols;
+    cols.row0 = a.row_begin + t * TILE;
+    cols.valid = static_cast<int>((nrows - t * TILE) < TILE ? (nrows - t * TILE) : TILE);
+    int32_t gid[ITEMS];
+    int64_t val[ITEMS];
+    const uint32_t alive = eval_query<THREADS, ITEMS>(q, cols, cols.valid, gid, val, a.err, pol_table);
+    if (!alive) continue;
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+      if (!((alive >> i) & 1u)) continue;
+      if (q.acc_mode == kAccSingle) {
+        my_sum += static_cast<uint64_t>(val[i]);
+        my_count += 1;
+      } else if (q.acc_mode == kAccShared) {
+        atomicAdd(acc.sums + gid[i], static_cast<unsigned long long>(val[i]));
+        atomicAdd(acc.counts + gid[i], 1u);
+      } else {
+        atomicAdd(q.sums + gid[i], static_cast<unsigned long long>(val[i]));
+        if (q.counts) atomicAdd(q.counts + gid[i], 1ull);
+      }
+    }
+  }
+  if (q.acc_mode == kAccSingle) {
+    const uint64_t s = block_sum_u64<THREADS>(my_sum, red);
+    const uint64_t c = block_sum_u64<THREADS>(my_count, red);
+    if (threadIdx.x == 0 && c) {
+      atomicAdd(q.sums, static_cast<unsigned long long>(s));
+      if (q.counts) atomicAdd(q.counts, static_cast<unsigned long long>(c));
+    }
+  } else if (q.acc_mode == kAccShared) {
+    __syncthreads();
+    flush_shared<THREADS>(acc, 0, q.groups, q.sums, q.counts);
+  }
+}
+
+// ------------------------------------------------------------------ shared scan
+
+constexpr int kScanMaxStages = 3;
+
+struct ScanArgs {
+  const int32_t* cols[CRYS_MAX_COLS];
+  int32_t slot_of[CRYS_MAX_COLS];     // table column -> staged slice, -1 if unused
+  int32_t union_cols[CRYS_MAX_COLS];  // staged slice -> table column
+  int32_t n_union;
+  int32_t stages;
+  int64_t row_begin, row_end;
+  int32_t n_queries;
+  int32_t shared_groups;  // accumulators held in shared memory, all queries
+  int32_t* err;
+  DevQuery q[CRYS_MAX_PLANS];
+};
+
+template <int THREADS, int ITEMS>
+__global__ void __launch_bounds__(THREADS) shared_scan_kernel(const __grid_constant__ ScanArgs a) {
+  constexpr int TILE = THREADS * ITEMS;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ StageRing<kScanMaxStages> ring;
+  const int S = a.stages;
+  const int tid = threadIdx.x, lane = tid % kWarp;
+  int32_t* stages = reinterpret_cast<int32_t*>(smem_raw);
+  const size_t stage_elems = static_cast<size_t>(a.n_union) * TILE;
+  const SharedAcc acc = shared_acc(smem_raw + S * stage_elems * sizeof(int32_t), a.shared_groups);
+  for (int g = tid; g < a.shared_groups; g += THREADS) {
+    acc.sums[g] = 0;
+    acc.counts[g] = 0;
+  }
+
+  const int64_t nrows = a.row_end - a.row_begin;
+  const int64_t ntiles = (nrows + TILE - 1) / TILE;
+  const uint64_t pol = policy_evict_first();
+  const uint64_t pol_table = policy_evict_last();
+  int64_t issued = 0;
+  const int32_t* ucols[CRYS_MAX_COLS];
+  for (int u = 0; u < a.n_union; ++u) ucols[u] = a.cols[a.union_cols[u]];
+
+  auto issue = [&](int s) {
+    const int64_t t = static_cast<int64_t>(blockIdx.x) + issued * gridDim.x;
+    ++issued;
+    if (t >= ntiles) {
+      ring.tile[s] = -1;
+      return;
+    }
+    ring.tile[s] = t;
+    const int64_t row = a.row_begin + t * TILE;
+    const int64_t valid = (nrows - t * TILE) < TILE ? (nrows - t * TILE) : TILE;
+    ring_issue(&ring.full[s], stages + s * stage_elems, TILE, ucols, a.n_union, row, valid, pol);
+  };
+
+  if (tid == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&ring.full[s], 1);
+      ring.tile[s] = -1;
+    }
+    fence_barrier_init();
+  }
+  __syncthreads();
+  if (tid == 0)
+    for (int s = 0; s < S; ++s) issue(s);
+  __syncthreads();
+
+  bool aborted = false;
+  for (int64_t k = 0;; ++k) {
+    const int s = static_cast<int>(k % S);
+    const int64_t t = ring.tile[s];
+    if (t < 0) break;
+    const bool ok = mbar_wait_bounded(&ring.full[s], static_cast<uint32_t>((k / S) & 1), a.err);
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) {
+        for (int j = 0; j < S; ++j) {
+          const int64_t kk = k + j;
+          const int ss = static_cast<int>(kk % S);
+          if (ring.tile[ss] >= 0)
+            mbar_wait_bounded(&ring.full[ss], static_cast<uint32_t>((kk / S) & 1), a.err);
+        }
+      }
+      aborted = true;
+      break;
+    }
+    StagedCols cols;
+    cols.cols = a.cols;
+    cols.slot_of = a.slot_of;
+    cols.stage = stages + s * stage_elems;
+    cols.tile = TILE;
+    cols.row0 = a.row_begin + t * TILE;
+    cols.valid = static_cast<int>((nrows - t * TILE) < TILE ? (nrows - t * TILE) : TILE);
+    cols.bulk = cols.valid & ~3;
+    for (int qi = 0; qi < a.n_queries; ++qi) {
+      const DevQuery& q = a.q[qi];
+      int32_t gid[ITEMS];
+      int64_t val[ITEMS];
+      const uint32_t alive = eval_query<THREADS, ITEMS>(q, cols, cols.valid, gid, val, a.err, pol_table);
+      if (q.acc_mode == kAccSingle) {
+        uint64_t s_sum = 0, s_cnt = 0;
+#pragma unroll
+        for (int i = 0; i < ITEMS; ++i) {
+          if ((alive >> i) & 1u) {
+            s_sum += static_cast<uint64_t>(val[i]);
+            s_cnt += 1;
+          }
+        }
+        s_sum = warp_sum_u64(s_sum);
+        s_cnt = warp_sum_u64(s_cnt);
+        if (lane == 0 && s_cnt) {
+          atomicAdd(acc.sums + q.acc_off, static_cast<unsigned long long>(s_sum));
+          atomicAdd(acc.counts + q.acc_off, static_cast<unsigned int>(s_cnt));
+        }
+      } else if (alive) {
+#pragma unroll
+        for (int i = 0; i < ITEMS; ++i) {
+          if (!((alive >> i) & 1u)) continue;
+          if (q.acc_mode == kAccShared) {
+            atomicAdd(acc.sums + q.acc_off + gid[i], static_cast<unsigned long long>(val[i]));
+            atomicAdd(acc.counts + q.acc_off + gid[i], 1u);
+          } else {
+            atomicAdd(q.sums + gid[i], static_cast<unsigned long long>(val[i]));
+            if (q.counts) atomicAdd(q.counts + gid[i], 1ull);
+          }
+        }
+      }
+    }
+    __syncthreads();
+    if (tid == 0) {
+      fence_proxy_async_smem();
+      issue(s);
+    }
+  }
+  if (aborted) return;
+  __syncthreads();
+  for (int qi = 0; qi < a.n_queries; ++qi) {
+    const DevQuery& q = a.q[qi];
+    if (q.acc_mode != kAccGlobal) flush_shared<THREADS>(acc, q.acc_off, q.groups, q.sums, q.counts);
+  }
+}
+
+// ------------------------------------------------------------------ host side
+
+constexpr int64_t kMaxGroups = 1ll << 28;
+constexpr size_t kSharedBudget = 200 * 1024;  // dynamic shared memory a block may use
+
+int groups_of(const crys_plan& p, int64_t* groups) {
+  if (p.n_joins < 0 || p.n_joins > CRYS_MAX_JOINS) return CRYS_EINVAL;
+  int64_t g = 1;
+  for (int j = 0; j < p.n_joins; ++j) {
+    const int32_t c = p.joins[j].group_card;
+    if (c < 0) return CRYS_EINVAL;
+    if (c > 0) {
+      g *= c;
+      if (g > kMaxGroups) return CRYS_EINVAL;
+    }
+  }
+  *groups = g;
+  return CRYS_OK;
+}
+
+int to_device(const crys_table& t, const crys_plan& p, DevQuery* d, uint32_t* col_mask) {
+  int64_t groups = 0;
+  if (groups_of(p, &groups) != CRYS_OK) return CRYS_EINVAL;
+  if (p.n_preds < 0 || p.n_preds > CRYS_MAX_PREDS) return CRYS_EINVAL;
+  if (p.agg_op < CRYS_AGG_A || p.agg_op > CRYS_AGG_A_ADD_B) return CRYS_EINVAL;
+  if (!p.d_sums) return CRYS_EINVAL;
+  auto col_ok = [&](int32_t c) { return c >= 0 && c < t.n_cols; };
+  uint32_t mask = 0;
+  d->n_preds = p.n_preds;
+  for (int f = 0; f < p.n_preds; ++f) {
+    if (!col_ok(p.preds[f].col)) return CRYS_EINVAL;
+    d->pred_col[f] = p.preds[f].col;
+    d->pred_lo[f] = p.preds[f].lo;
+    d->pred_hi[f] = p.preds[f].hi;
+    mask |= 1u << p.preds[f].col;
+  }
+  d->n_joins = p.n_joins;
+  for (int j = 0; j < p.n_joins; ++j) {
+    const crys_join& J = p.joins[j];
+    if (!col_ok(J.fk_col) || !J.ht.slots || !is_pow2(J.ht.capacity) || J.ht.capacity < 2 ||
+        J.ht.capacity > (1ll << 31))
+      return CRYS_EINVAL;
+    d->joins[j].slots = J.ht.slots;
+    d->joins[j].mask = static_cast<uint32_t>(J.ht.capacity - 1);
+    d->joins[j].shift = 32u - log2_pow2(static_cast<uint64_t>(J.ht.capacity));
+    d->joins[j].fk_col = J.fk_col;
+    d->joins[j].card = J.group_card;
+    mask |= 1u << J.fk_col;
+  }
+  if (!col_ok(p.agg_a)) return CRYS_EINVAL;
+  mask |= 1u << p.agg_a;
+  if (p.agg_op != CRYS_AGG_A) {
+    if (!col_ok(p.agg_b)) return CRYS_EINVAL;
+    mask |= 1u << p.agg_b;
+  }
+  d->agg_op = p.agg_op;
+  d->agg_a = p.agg_a;
+  d->agg_b = p.agg_op != CRYS_AGG_A ? p.agg_b : p.agg_a;
+  d->groups = groups;
+  d->sums = reinterpret_cast<unsigned long long*>(p.d_sums);
+  d->counts = reinterpret_cast<unsigned long long*>(p.d_counts);
+  d->acc_mode = kAccGlobal;
+  d->acc_off = 0;
+  *col_mask = mask;
+  return CRYS_OK;
+}
+
+int check_table(const crys_table* t) {
+  if (!t || t->n_cols < 1 || t->n_cols > CRYS_MAX_COLS || t->n_rows < 0) return CRYS_EINVAL;
+  for (int c = 0; c < t->n_cols; ++c)
+    if (t->n_rows > 0 && (!t->cols[c] || !aligned16(t->cols[c]))) return CRYS_EINVAL;
+  return CRYS_OK;
+}
+
+int zero_outputs(const DevQuery& q, cudaStream_t s) {
+  if (cudaMemsetAsync(q.sums, 0, static_cast<size_t>(q.groups) * 8, s) != cudaSuccess) return CRYS_ECUDA;
+  if (q.counts && cudaMemsetAsync(q.counts, 0, static_cast<size_t>(q.groups) * 8, s) != cudaSuccess)
+    return CRYS_ECUDA;
+  return CRYS_OK;
+}
+
+// Per-block accumulators are 32-bit counts: a block must see fewer than 2^32 rows.
+bool counts_fit(int64_t rows, int grid) { return (rows / (grid > 0 ? grid : 1)) + (1 << 16) < (1ll << 32); }
+
+template <int THREADS, int ITEMS>
+int launch_plan(PlanArgs& a, cudaStream_t s) {
+  constexpr int TILE = THREADS * ITEMS;
+  size_t smem = 0;
+  if (a.q.groups == 1) {
+    a.q.acc_mode = kAccSingle;
+  } else if (static_cast<size_t>(a.q.groups) * 12 <= kSharedBudget) {
+    a.q.acc_mode = kAccShared;
+    smem = static_cast<size_t>(a.q.groups) * 12;
+  } else {
+    a.q.acc_mode = kAccGlobal;
+  }
+  auto k = plan_kernel<THREADS, ITEMS>;
+  if (!allow_smem(k, smem)) return CRYS_ECUDA;
+  const int64_t ntiles = (a.row_end - a.row_begin + TILE - 1) / TILE;
+  const int grid = persistent_grid(k, THREADS, smem, ntiles);
+  if (!counts_fit(a.row_end - a.row_begin, grid)) return CRYS_EINVAL;
+  k<<<grid, THREADS, smem, s>>>(a);
+  note_launch();
+  return check_launch();
+}
+
+template <int THREADS, int ITEMS>
+int launch_scan(ScanArgs& a, cudaStream_t s) {
+  constexpr int TILE = THREADS * ITEMS;
+  const size_t stage_bytes = static_cast<size_t>(a.n_union) * TILE * sizeof(int32_t);
+  // Shared-memory accumulators for as many queries as fit next to two stages; the rest
+  // accumulate with global atomics.  Single-group queries always take one slot.
+  const size_t budget = kSharedBudget > 2 * stage_bytes ? kSharedBudget - 2 * stage_bytes : 0;
+  int64_t used = 0;
+  for (int qi = 0; qi < a.n_queries; ++qi) {
+    DevQuery& q = a.q[qi];
+    if (static_cast<size_t>(used + q.groups) * 12 <= budget) {
+      q.acc_mode = q.groups == 1 ? kAccSingle : kAccShared;
+      q.acc_off = static_cast<int32_t>(used);
+      used += q.groups;
+    } else {
+      q.acc_mode = kAccGlobal;
+    }
+  }
+  a.shared_groups = static_cast<int32_t>(used);
+  const size_t acc_bytes = static_cast<size_t>(used) * 12;
+  a.stages = (3 * stage_bytes + acc_bytes <= kSharedBudget) ? 3 : 2;
+  const size_t smem = a.stages * stage_bytes + acc_bytes;
+  if (smem > 227 * 1024) return CRYS_EINVAL;
+  auto k = shared_scan_kernel<THREADS, ITEMS>;
+  if (!allow_smem(k, smem)) return CRYS_ECUDA;
+  const int64_t ntiles = (a.row_end - a.row_begin + TILE - 1) / TILE;
+  const int grid = persistent_grid(k, THREADS, smem, ntiles);
+  if (!counts_fit(a.row_end - a.row_begin, grid)) return CRYS_EINVAL;
+  k<<<grid, THREADS, smem, s>>>(a);
+  note_launch();
+  return check_launch();
+}
+
+}  // namespace
+}  // namespace crys
+
+extern "C" {
+
+int crys_plan_groups(const crys_plan* plan, int64_t* groups) {
+  if (!plan || !groups) return CRYS_EINVAL;
+  return crys::groups_of(*plan, groups);
+}
+
+int crys_run_plan(const crys_table* fact, const crys_plan* plan, crys_stream stream) {
+  using namespace crys;
+  if (check_table(fact) != CRYS_OK || !plan) return CRYS_EINVAL;
+  static PlanArgs zero_args;  // zero-initialised template
+  PlanArgs a = zero_args;
+  uint32_t mask = 0;
+  if (to_device(*fact, *plan, &a.q, &mask) != CRYS_OK) return CRYS_EINVAL;
+  for (int c = 0; c < fact->n_cols; ++c) a.cols[c] = fact->cols[c];
+  a.row_begin = 0;
+  a.row_end = fact->n_rows;
+  a.err = device_error_word();
+  if (!a.err) return CRYS_ECUDA;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (zero_outputs(a.q, s) != CRYS_OK) return CRYS_ECUDA;
+  if (fact->n_rows == 0) return CRYS_OK;
+  constexpr int kOp = CRYS_OP_PLAN;
+  switch (tile_variant(kOp)) {
+    case 1: return launch_plan<kTiles[kOp][1].threads, kTiles[kOp][1].items>(a, s);
+    case 2: return launch_plan<kTiles[kOp][2].threads, kTiles[kOp][2].items>(a, s);
+    case 3: return launch_plan<kTiles[kOp][3].threads, kTiles[kOp][3].items>(a, s);
+    default: return launch_plan<kTiles[kOp][0].threads, kTiles[kOp][0].items>(a, s);
+  }
+}
+
+int crys_run_plans(const crys_table* fact, const crys_plan* plans, int32_t n_plans,
+                   int64_t row_begin, int64_t row_end, int flags, crys_stream stream) {
+  using namespace crys;
+  if (check_table(fact) != CRYS_OK || n_plans < 0 || n_plans > CRYS_MAX_PLANS) return CRYS_EINVAL;
+  if (n_plans > 0 && !plans) return CRYS_EINVAL;
+  if (row_begin < 0 || row_end < row_begin || row_end > fact->n_rows || (row_begin & 3)) return CRYS_EINVAL;
+  if (flags & ~CRYS_ACCUMULATE) return CRYS_EINVAL;
+  static ScanArgs zero_args;
+  ScanArgs* a = new ScanArgs(zero_args);
+  uint32_t mask = 0;
+  for (int qi = 0; qi < n_plans; ++qi) {
+    uint32_t m = 0;
+    if (to_device(*fact, plans[qi], &a->q[qi], &m) != CRYS_OK) {
+      delete a;
+      return CRYS_EINVAL;
+    }
+    mask |= m;
+  }
+  a->n_queries = n_plans;
+  a->n_union = 0;
+  for (int c = 0; c < CRYS_MAX_COLS; ++c) {
+    a->cols[c] = c < fact->n_cols ? fact->cols[c] : nullptr;
+    a->slot_of[c] = -1;
+    if (mask & (1u << c)) {
+      a->slot_of[c] = a->n_union;
+      a->union_cols[a->n_union++] = c;
+    }
+  }
+  a->row_begin = row_begin;
+  a->row_end = row_end;
+  a->err = device_error_word();
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  int rc = a->err ? CRYS_OK : CRYS_ECUDA;
+  if (rc == CRYS_OK && !(flags & CRYS_ACCUMULATE)) {
+    for (int qi = 0; qi < n_plans && rc == CRYS_OK; ++qi) rc = zero_outputs(a->q[qi], s);
+  }
+  if (rc == CRYS_OK && n_plans > 0 && row_end > row_begin) {
+    constexpr int kOp = CRYS_OP_SHARED_SCAN;
+    switch (tile_variant(kOp)) {
+      case 1: rc = launch_scan<kTiles[kOp][1].threads, kTiles[kOp][1].items>(*a, s); break;
+      case 2: rc = launch_scan<kTiles[kOp][2].threads, kTiles[kOp][2].items>(*a, s); break;
+      case 3: rc = launch_scan<kTiles[kOp][3].threads, kTiles[kOp][3].items>(*a, s); break;
+      default: rc = launch_scan<kTiles[kOp][0].threads, kTiles[kOp][0].items>(*a, s); break;
+    }
+  }
+  delete a;
+  return rc;
+}
+
+}  // extern "C"

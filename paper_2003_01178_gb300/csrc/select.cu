@@ -1,0 +1,284 @@
+// Selection (Section 3.2 query Q0, Section 4.2 query Q3) as one persistent kernel.
+//
+// Per tile: BlockLoad (bulk copy into a shared-memory stage) -> BlockPred (range
+// predicate into a per-thread bitmap in registers) -> BlockScan (warp scans of packed
+// per-thread counts, then one warp scans the per-warp segment totals) -> one output
+// reservation per tile -> BlockShuffle (compaction in place in the stage) ->
+// BlockStore (coalesced stores of the compacted run).
+//
+// Each thread reads 4-value groups j*THREADS + tid (j < ITEMS/4) of the tile, so a
+// warp's group j is 128 consecutive rows; segments (j, warp) are therefore in input
+// order and the compacted tile keeps input order.
+//
+// Output reservation: mode 0 adds the tile's count to the global cursor with one
+// atomic (the paper's scheme); mode 1 chains tiles with a decoupled look-back (tile
+// ids handed out in order by an atomic counter, so a tile only waits on tiles that
+// running blocks already hold) and the result is in input order.
+#include "common.cuh"
+#include "pipeline.cuh"
+#include "tiles.h"
+
+namespace crys {
+namespace {
+
+constexpr int kStages = 3;
+constexpr uint64_t kFlagAggregate = 1ull << 62;
+constexpr uint64_t kFlagInclusive = 2ull << 62;
+constexpr uint64_t kValueMask = (1ull << 62) - 1;
+
+struct SelectArgs {
+  const int32_t* x;
+  int64_t n;
+  int32_t lo, hi;
+  int32_t* out;
+  unsigned long long* count;  // cursor (mode 0) / final count (mode 1)
+  uint64_t* tile_state;       // mode 1: one status word per tile
+  unsigned int* tile_counter; // mode 1: next tile id
+  int32_t* err;
+};
+
+// Decoupled look-back over tiles 0..t-1 (thread 0 only).  Returns the number of
+// selected rows in all earlier tiles, or -1 if a predecessor never published within
+// the wait bound (or another block already reported a failure).
+__device__ int64_t lookback_exclusive(uint64_t* state, int64_t t, uint64_t total, int32_t* err) {
+  if (t == 0) {
+    st_relaxed_u64(&state[0], kFlagInclusive | total);
+    return 0;
+  }
+  st_relaxed_u64(&state[t], kFlagAggregate | total);
+  uint64_t excl = 0;
+  int64_t p = t - 1;
+  uint64_t t0 = 0;
+  bool timing = false;
+  while (p >= 0) {
+    const uint64_t w = ld_relaxed_u64(&state[p]);
+    const uint64_t flag = w >> 62;
+    if (flag == 0) {
+      if (!timing) {
+        t0 = global_timer_ns();
+        timing = true;
+      } else if (global_timer_ns() - t0 > kWaitBoundNs) {
+        set_error(err, CRYS_DEV_TIMEOUT);
+        return -1;
+      }
+      if (read_error(err) & CRYS_DEV_TIMEOUT) return -1;
+      continue;
+    }
+    timing = false;
+    excl += w & kValueMask;
+    if (flag == 2) break;
+    --p;
+  }
+  st_relaxed_u64(&state[t], kFlagInclusive | (excl + total));
+  return static_cast<int64_t>(excl);
+}
+
+template <int THREADS, int ITEMS, bool ORDERED>
+__global__ void __launch_bounds__(THREADS) select_kernel(SelectArgs a) {
+  constexpr int TILE = THREADS * ITEMS;
+  constexpr int VEC = ITEMS / 4;
+  constexpr int WARPS = THREADS / kWarp;
+  constexpr int NSEG = VEC * WARPS;
+  static_assert(ITEMS % 4 == 0 && VEC <= 4, "4..16 items per thread");
+
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  int32_t* stages = reinterpret_cast<int32_t*>(smem_raw);
+  __shared__ StageRing<kStages> ring;
+  __shared__ int32_t seg[NSEG + 1];
+  __shared__ long long out_base;
+
+  const int tid = threadIdx.x, lane = tid % kWarp, warp = tid / kWarp;
+  const int64_t ntiles = (a.n + TILE - 1) / TILE;
+  const uint64_t pol = policy_evict_first();
+  int64_t issued = 0;  // thread 0 only
+
+  auto issue = [&](int s) {
+    int64_t t = ORDERED ? static_cast<int64_t>(atomicAdd(a.tile_counter, 1u))
+                        : static_cast<int64_t>(blockIdx.x) + issued * gridDim.x;
+    ++issued;
+    if (t >= ntiles) {
+      ring.tile[s] = -1;
+      return;
+    }
+    ring.tile[s] = t;
+    const int64_t row = t * TILE;
+    const int64_t valid = (a.n - row) < TILE ? (a.n - row) : TILE;
+    ring_issue(&ring.full[s], stages + s * TILE, TILE, &a.x, 1, row, valid, pol);
+  };
+
+  ring_init(ring);
+  if (tid == 0)
+    for (int s = 0; s < kStages; ++s) issue(s);
+  __syncthreads();
+
+  for (int64_t k = 0;; ++k) {
+    const int s = static_cast<int>(k % kStages);
+    const int64_t t = ring.tile[s];
+    if (t < 0) break;
+    if (!ring_wait(ring, k, a.err)) {
+      if (tid == 0) ring_drain(ring, k, a.err);
+      return;
+    }
+    int32_t* st = stages + s * TILE;
+    const int64_t row0 = t * TILE;
+    const int valid = static_cast<int>((a.n - row0) < TILE ? (a.n - row0) : TILE);
+    const int bulk = valid & ~3;
+
+    // BlockLoad + BlockPred: values and bitmap in registers.
+    int32_t v[ITEMS];
+    uint32_t bits = 0;
+#pragma unroll
+    for (int j = 0; j < VEC; ++j) {
+      const int p = (j * THREADS + tid) * 4;
+      const int4 q = stage_read4(st, a.x + row0, p, bulk, valid);
+      v[4 * j + 0] = q.x;
+      v[4 * j + 1] = q.y;
+      v[4 * j + 2] = q.z;
+      v[4 * j + 3] = q.w;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const bool hit = (p + e < valid) && v[4 * j + e] >= a.lo && v[4 * j + e] <= a.hi;
+        bits |= static_cast<uint32_t>(hit) << (4 * j + e);
+      }
+    }
+    // BlockScan, level 1: one warp scan of the per-thread counts of all VEC groups at
+    // once (group j's count in byte j; a warp's group total is at most 128).
+    uint32_t packed = 0;
+#pragma unroll
+    for (int j = 0; j < VEC; ++j) packed |= static_cast<uint32_t>(__popc((bits >> (4 * j)) & 0xFu)) << (8 * j);
+    const uint32_t incl = static_cast<uint32_t>(warp_inclusive_scan(static_cast<int32_t>(packed), lane));
+    const uint32_t excl = incl - packed;
+    if (lane == kWarp - 1) {
+#pragma unroll
+      for (int j = 0; j < VEC; ++j) seg[j * WARPS + warp] = static_cast<int32_t>((incl >> (8 * j)) & 0xFFu);
+    }
+    __syncthreads();
+    // Level 2: warp 0 scans the NSEG segment totals (in input order) and reserves the
+    // tile's output range.
+    if (warp == 0) {
+      int32_t carry = 0;
+      for (int c0 = 0; c0 < NSEG; c0 += kWarp) {
+        const int32_t x = (c0 + lane < NSEG) ? seg[c0 + lane] : 0;
+        const int32_t inc = warp_inclusive_scan(x, lane);
+        if (c0 + lane < NSEG) seg[c0 + lane] = carry + inc - x;
+        carry += __shfl_sync(0xFFFFFFFFu, inc, kWarp - 1);
+      }
+      if (lane == 0) {
+        seg[NSEG] = carry;
+        long long base;
+        if (ORDERED) {
+          base = lookback_exclusive(a.tile_state, t, static_cast<uint64_t>(carry), a.err);
+          if (base >= 0 && t == ntiles - 1) *a.count = static_cast<unsigned long long>(base + carry);
+        } else {
+          base = carry ? static_cast<long long>(atomicAdd(a.count, static_cast<unsigned long long>(carry))) : 0;
+        }
+        out_base = base;
+      }
+    }
+    __syncthreads();
+    const long long base = out_base;
+    const int total = seg[NSEG];
+    if (base < 0) {  // look-back gave up: abandon uniformly
+      if (tid == 0) ring_drain(ring, k, a.err);
+      return;
+    }
+    // BlockShuffle: compact the selected values in place (every thread already holds
+    // its values in registers, and the scan's barrier ordered all stage reads first).
+#pragma unroll
+    for (int j = 0; j < VEC; ++j) {
+      int pos = seg[j * WARPS + warp] + static_cast<int>((excl >> (8 * j)) & 0xFFu);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        if (bits & (1u << (4 * j + e))) st[pos++] = v[4 * j + e];
+      }
+    }
+    __syncthreads();
+    // BlockStore: coalesced copy of the compacted run to out[base, base + total).
+    if (base + total <= a.n) {
+      for (int i = tid; i < total; i += THREADS) a.out[base + i] = st[i];
+    } else if (tid == 0) {
+      set_error(a.err, CRYS_DEV_BOUNDS);
+    }
+    __syncthreads();
+    if (tid == 0) {
+      fence_proxy_async_smem();
+      issue(s);
+    }
+  }
+}
+
+template <int THREADS, int ITEMS>
+int launch(const SelectArgs& a, bool ordered, cudaStream_t s) {
+  constexpr int TILE = THREADS * ITEMS;
+  const size_t smem = static_cast<size_t>(kStages) * TILE * sizeof(int32_t);
+  const int64_t ntiles = (a.n + TILE - 1) / TILE;
+  if (ordered) {
+    auto k = select_kernel<THREADS, ITEMS, true>;
+    if (!allow_smem(k, smem)) return CRYS_ECUDA;
+    k<<<persistent_grid(k, THREADS, smem, ntiles), THREADS, smem, s>>>(a);
+  } else {
+    auto k = select_kernel<THREADS, ITEMS, false>;
+    if (!allow_smem(k, smem)) return CRYS_ECUDA;
+    k<<<persistent_grid(k, THREADS, smem, ntiles), THREADS, smem, s>>>(a);
+  }
+  note_launch();
+  return check_launch();
+}
+
+constexpr int kOp = CRYS_OP_SELECT;
+
+int64_t min_tile() {
+  int64_t m = INT64_MAX;
+  for (int i = 0; i < kNumVariants[kOp]; ++i) {
+    const int64_t t = static_cast<int64_t>(kTiles[kOp][i].threads) * kTiles[kOp][i].items;
+    if (t < m) m = t;
+  }
+  return m;
+}
+
+}  // namespace
+}  // namespace crys
+
+extern "C" int crys_select(const int32_t* x, int64_t n, int32_t lo, int32_t hi, int32_t* out,
+                           int64_t* d_count, int order_preserving, void* d_temp,
+                           size_t* temp_bytes, crys_stream stream) {
+  using namespace crys;
+  if (n < 0 || (order_preserving != 0 && order_preserving != 1)) return CRYS_EINVAL;
+  const int64_t max_tiles = (n + min_tile() - 1) / min_tile();
+  const size_t need = order_preserving ? (static_cast<size_t>(max_tiles) * 8 + 256) : 0;
+  if (!d_temp && temp_bytes) {
+    *temp_bytes = need;
+    return CRYS_OK;
+  }
+  if (need && (!d_temp || !temp_bytes)) return CRYS_EINVAL;
+  if (need && *temp_bytes < need) return CRYS_ENOMEM;
+  if (!d_count || (n > 0 && (!x || !out))) return CRYS_EINVAL;
+  if (n > 0 && !aligned16(x)) return CRYS_EINVAL;
+  if (need && (reinterpret_cast<uintptr_t>(d_temp) & 255u)) return CRYS_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (cudaMemsetAsync(d_count, 0, sizeof(int64_t), s) != cudaSuccess) return CRYS_ECUDA;
+  if (n == 0) return CRYS_OK;
+  SelectArgs a;
+  a.x = x;
+  a.n = n;
+  a.lo = lo;
+  a.hi = hi;
+  a.out = out;
+  a.count = reinterpret_cast<unsigned long long*>(d_count);
+  a.tile_counter = nullptr;
+  a.tile_state = nullptr;
+  a.err = device_error_word();
+  if (!a.err) return CRYS_ECUDA;
+  if (order_preserving) {
+    a.tile_counter = static_cast<unsigned int*>(d_temp);
+    a.tile_state = reinterpret_cast<uint64_t*>(static_cast<char*>(d_temp) + 256);
+    if (cudaMemsetAsync(d_temp, 0, need, s) != cudaSuccess) return CRYS_ECUDA;
+  }
+  const bool ord = order_preserving != 0;
+  switch (tile_variant(CRYS_OP_SELECT)) {
+    case 1: return launch<kTiles[kOp][1].threads, kTiles[kOp][1].items>(a, ord, s);
+    case 2: return launch<kTiles[kOp][2].threads, kTiles[kOp][2].items>(a, ord, s);
+    case 3: return launch<kTiles[kOp][3].threads, kTiles[kOp][3].items>(a, ord, s);
+    default: return launch<kTiles[kOp][0].threads, kTiles[kOp][0].items>(a, ord, s);
+  }
+}

@@ -1,0 +1,140 @@
+"""Select-join-group-by queries over a star schema resident in HBM (Section 5.3).
+
+A query (plain dict: fact predicates, joins with dimension filters and an optional
+group attribute per dimension, one SUM expression) is compiled into the paper's plan
+shape: one build kernel per joined dimension (the dimension filter applied at build
+time, the group attribute as the table's value) and one fused probe kernel over the
+fact table.  Queries over the same fact table can also share one scan
+(``crys_run_plans``).  Hash tables are sized from the filter's expected selectivity
+with a large safety margin; the build flags a full table on the device and
+``check_device_errors`` raises, so a wrong estimate can never go unnoticed.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import torch
+
+from . import (HashTable, crys_hash_build, crys_hash_init, crys_run_plan, crys_run_plans,
+               make_plan, make_table, capacity_for, ACCUMULATE, MAX_PLANS)
+
+
+@dataclass
+class Schema:
+    """Names and domains of the fact columns and of each dimension's attributes."""
+    fact_cols: list
+    dims: dict          # dim -> {"fk": fact col name, "attrs": {attr: cardinality}}
+
+
+@dataclass
+class CompiledQuery:
+    query: dict
+    plan: object                       # crys_plan
+    sums: torch.Tensor
+    counts: torch.Tensor
+    tables: list = field(default_factory=list)   # HashTables kept alive with the plan
+    groups: int = 1
+
+    @property
+    def table_bytes(self) -> int:
+        return sum(t.nbytes for t in self.tables)
+
+    @property
+    def output_bytes(self) -> int:
+        return 16 * self.groups
+
+
+class ResidentStarSchema:
+    """Fact and dimension columns kept resident on one device."""
+
+    def __init__(self, schema: Schema, fact: dict, dims: dict):
+        self.schema = schema
+        self.fact = fact
+        self.dims = dims
+        self.cols = [fact[c] for c in schema.fact_cols]
+        self.table = make_table(self.cols)
+        self.n_rows = self.cols[0].numel()
+        self.device = self.cols[0].device
+
+    # -- sizing -------------------------------------------------------------------
+    def expected_rows(self, join: dict) -> float:
+        d = join["dim"]
+        rows = self.dims[d]["key"].numel()
+        sel = 1.0
+        for attr, lo, hi in join["filters"]:
+            sel *= (hi - lo + 1) / self.schema.dims[d]["attrs"][attr]
+        return rows * sel
+
+    def table_capacity(self, join: dict) -> int:
+        mean = self.expected_rows(join)
+        bound = mean + 8.0 * math.sqrt(mean) + 64
+        rows = self.dims[join["dim"]]["key"].numel()
+        return capacity_for(int(min(rows, bound)))
+
+    def memory_needed(self, query: dict) -> int:
+        """Device bytes a query holds while admitted: its hash tables and outputs."""
+        tb = sum(8 * self.table_capacity(j) for j in query["joins"])
+        return tb + 16 * self.groups(query)
+
+    def groups(self, query: dict) -> int:
+        g = 1
+        for j in query["joins"]:
+            if j["group"] is not None:
+                g *= self.schema.dims[j["dim"]]["attrs"][j["group"]]
+        return g
+
+    # -- compilation ----------------------------------------------------------------
+    def compile(self, query: dict, stream=None) -> CompiledQuery:
+        names = self.schema.fact_cols
+        preds = [(names.index(c), lo, hi) for (c, lo, hi) in query["fact_preds"]]
+        joins, tables = [], []
+        for j in query["joins"]:
+            d = j["dim"]
+            dim = self.dims[d]
+            spec = self.schema.dims[d]
+            ht = HashTable(self.table_capacity(j), self.device)
+            crys_hash_init(ht.struct, stream)
+            filters = [(dim[a], lo, hi) for (a, lo, hi) in j["filters"]]
+            vals = dim[j["group"]] if j["group"] is not None else None
+            crys_hash_build(dim["key"], vals, dim["key"].numel(), filters, ht.struct, stream)
+            card = spec["attrs"][j["group"]] if j["group"] is not None else 0
+            joins.append((names.index(spec["fk"]), ht, card))
+            tables.append(ht)
+        op, a, b = query["agg"]
+        agg = (op, names.index(a), names.index(b) if b is not None else None)
+        g = self.groups(query)
+        sums = torch.zeros(g, dtype=torch.int64, device=self.device)
+        counts = torch.zeros(g, dtype=torch.int64, device=self.device)
+        plan = make_plan(preds, joins, agg, sums, counts)
+        return CompiledQuery(query, plan, sums, counts, tables, g)
+
+    # -- execution ------------------------------------------------------------------
+    def run(self, cq: CompiledQuery, stream=None) -> None:
+        """One query, one fused probe kernel over all fact rows."""
+        crys_run_plan(self.table, cq.plan, stream)
+
+    def run_shared(self, cqs: list, row_begin: int = 0, row_end: int | None = None,
+                   accumulate: bool = False, stream=None) -> None:
+        """Up to 32 queries in one shared scan over rows [row_begin, row_end)."""
+        if len(cqs) > MAX_PLANS:
+            raise ValueError("at most 32 queries per shared scan")
+        row_end = self.n_rows if row_end is None else row_end
+        crys_run_plans(self.table, [c.plan for c in cqs], row_begin, row_end,
+                       ACCUMULATE if accumulate else 0, stream)
+
+    def bytes_scanned(self, query: dict) -> int:
+        """Algorithmic bytes of one query: each fact column it reads, once (4 B/row)."""
+        cols = {c for (c, _, _) in query["fact_preds"]}
+        cols |= {self.schema.dims[j["dim"]]["fk"] for j in query["joins"]}
+        op, a, b = query["agg"]
+        cols.add(a)
+        if b is not None:
+            cols.add(b)
+        return 4 * self.n_rows * len(cols)
+
+
+def served_schema() -> Schema:
+    import datagen
+    return Schema(list(datagen.SS_FACT_COLS),
+                  {d: {"fk": s["fk"], "attrs": dict(s["attrs"])} for d, s in datagen.SS_DIMS.items()})

@@ -1,0 +1,96 @@
+"""The C-ABI library loads and exports every symbol include/crystal.h declares; host-side
+argument checks answer without touching a GPU."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def crys():
+    from paper_2003_01178_gb300 import _build
+    _build.build()
+    import paper_2003_01178_gb300 as crys
+    crys.lib()
+    return crys
+
+
+def _declared():
+    text = open(os.path.join(ROOT, "include", "crystal.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(crys_[a-z_]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(crys):
+    names = _declared()
+    assert len(names) >= 15
+    L = crys.lib()
+    for n in names:
+        assert hasattr(L, n), n
+
+
+def test_strerror_and_tiles(crys):
+    assert crys.strerror(crys.OK) == "ok"
+    assert "argument" in crys.strerror(crys.EINVAL)
+    for op in range(6):
+        v = crys.crys_tile_variants(op)
+        assert 1 <= len(v) <= 4 and all(t % 32 == 0 and i > 0 for t, i in v)
+    assert crys.crys_tile_variants(0)[3] == (128, 4)      # the paper's tile shape is available
+    with pytest.raises(crys.CrystalError):
+        crys.crys_set_tile(0, 99)
+    crys.crys_set_tile(0, 1)
+    assert crys.crys_get_tile(0) == 1
+    crys.crys_set_tile(0, 0)
+
+
+def test_host_side_validation_without_gpu(crys):
+    L = crys.lib()
+    size = C.c_size_t(0)
+    # size queries
+    assert L.crys_select(None, 1000, 0, 1, None, None, 1, None, C.byref(size), None) == crys.OK
+    assert size.value >= 8
+    assert L.crys_select(None, 1000, 0, 1, None, None, 0, None, C.byref(size), None) == crys.OK
+    assert size.value == 0
+    assert L.crys_sort(None, None, None, None, 1 << 20, None, C.byref(size), None) == crys.OK
+    assert size.value >= 8 * (1 << 20)
+    # rejected before any launch
+    assert L.crys_select(None, -1, 0, 1, None, None, 0, None, None, None) == crys.EINVAL
+    assert L.crys_select(None, 10, 0, 1, None, None, 2, None, None, None) == crys.EINVAL
+    assert L.crys_project(None, None, 10, 1.0, 1.0, 5, None, None) == crys.EINVAL
+    assert L.crys_project(C.c_void_p(16), C.c_void_p(16), 10, 1.0, 1.0, 0, C.c_void_p(20), None) == crys.EINVAL
+    bad = crys.crys_hash(C.c_void_p(4096), 3)
+    assert L.crys_hash_init(C.byref(bad), None) == crys.EINVAL
+    assert L.crys_sort(None, None, None, None, 1 << 31, None, None, None) == crys.EINVAL
+    ok = crys.crys_hash(C.c_void_p(4096), 8)
+    assert L.crys_hash_build(C.c_void_p(4096), None, 100, None, 0, C.byref(ok), None) == crys.EFULL
+    plan = crys.crys_plan()
+    plan.n_joins = 2
+    plan.joins[0].group_card = 100
+    plan.joins[1].group_card = 7
+    g = C.c_int64(0)
+    assert L.crys_plan_groups(C.byref(plan), C.byref(g)) == crys.OK and g.value == 700
+    plan.joins[1].group_card = -1
+    assert L.crys_plan_groups(C.byref(plan), C.byref(g)) == crys.EINVAL
+    t = crys.crys_table()
+    t.n_cols = 0
+    assert L.crys_run_plan(C.byref(t), C.byref(plan), None) == crys.EINVAL
+    assert L.crys_run_plans(C.byref(t), None, 40, 0, 0, 0, None) == crys.EINVAL
+
+
+def test_generator_library_exports(crys):
+    import datagen.device as dgd
+    L = dgd.lib()
+    for n in ("dg_uniform_i32", "dg_uniform_f32", "dg_bits_i32", "dg_perm_i32"):
+        assert hasattr(L, n)
+
+
+def test_product_does_not_import_oracle():
+    import subprocess
+    import sys
+    code = ("import sys; sys.path.insert(0, %r); import paper_2003_01178_gb300, "
+            "paper_2003_01178_gb300.starschema, paper_2003_01178_gb300.server; "
+            "assert 'oracle' not in sys.modules, 'oracle imported'" % ROOT)
+    subprocess.check_call([sys.executable, "-c", code])

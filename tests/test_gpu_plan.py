@@ -1,0 +1,142 @@
+"""GPU parity of the fused select-join-aggregate kernels (one query, and the shared scan
+of several queries) against the oracle, through the C ABI."""
+import numpy as np
+import pytest
+
+import datagen
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+I32_MIN = -(1 << 31)
+
+
+@pytest.fixture(scope="module")
+def crys():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2003_01178_gb300 import _build
+    _build.build()
+    import paper_2003_01178_gb300 as crys
+    crys.crys_device_errors(clear=True)
+    yield crys
+    assert crys.crys_device_errors(clear=True) == 0
+    for op in range(6):
+        crys.crys_set_tile(op, 0)
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _q1_gpu(crys, fact, dim, year=3):
+    ht = crys.HashTable.build(dim["key"], dim["yr"], filters=[(dim["yr"], year, year)])
+    sums, counts = crys.run_plan([fact["fk"], fact["a"], fact["b"], fact["c"]],
+                                 [(1, I32_MIN, 24), (2, 1, 3)], [(0, ht, 0)], ("mul", 3, 2))
+    return int(sums[0].item()), int(counts[0].item())
+
+
+@pytest.mark.parametrize("n", [0, 1, 5, 1023, 4096, 4099, 100_003, 1 << 22])
+@pytest.mark.parametrize("variant", range(4))
+def test_q1_parity(crys, orc, n, variant):
+    crys.crys_set_tile(crys.OP_PLAN, variant)
+    host = datagen.q1_tables(40 + n % 7, n)
+    fact = {k: _dev(v) for k, v in host["fact"].items()}
+    dim = {k: _dev(v) for k, v in host["dim"].items()}
+    s, c = _q1_gpu(crys, fact, dim)
+    assert s == orc.q1_run(host["fact"], host["dim"])
+    crys.crys_set_tile(crys.OP_PLAN, 0)
+
+
+def test_q1_year_invariant_on_gpu(crys, orc):
+    host = datagen.q1_tables(77, 1 << 20)
+    fact = {k: _dev(v) for k, v in host["fact"].items()}
+    dim = {k: _dev(v) for k, v in host["dim"].items()}
+    per_year = [_q1_gpu(crys, fact, dim, y)[0] for y in range(7)]
+    assert per_year == [orc.q1_run(host["fact"], host["dim"], y) for y in range(7)]
+
+
+def _schema_tables(seed, n, scale):
+    host = datagen.ss_tables(seed, n, dim_scale=scale)
+    fact = {k: _dev(v) for k, v in host["fact"].items()}
+    dims = {d: {k: _dev(v) for k, v in t.items()} for d, t in host["dims"].items()}
+    return host, fact, dims
+
+
+@pytest.fixture(scope="module")
+def star(crys):
+    from paper_2003_01178_gb300.starschema import ResidentStarSchema, served_schema
+    host, fact, dims = _schema_tables(5, 300_007, 0.02)
+    return host, ResidentStarSchema(served_schema(), fact, dims)
+
+
+def _check(orc, host, cq, query):
+    rs, rc = orc.ss_run(host, query)
+    assert np.array_equal(cq.sums.cpu().numpy(), rs), query
+    assert np.array_equal(cq.counts.cpu().numpy(), rc), query
+
+
+@pytest.mark.parametrize("variant", range(4))
+def test_star_queries_one_at_a_time(crys, orc, star, variant):
+    crys.crys_set_tile(crys.OP_PLAN, variant)
+    host, ss = star
+    for qid in range(12):
+        q = datagen.ss_query(9, qid + 100 * variant)
+        cq = ss.compile(q)
+        ss.run(cq)
+        _check(orc, host, cq, q)
+    crys.check_device_errors()
+    crys.crys_set_tile(crys.OP_PLAN, 0)
+
+
+@pytest.mark.parametrize("variant", range(4))
+def test_shared_scan_equals_alone(crys, orc, star, variant):
+    crys.crys_set_tile(crys.OP_SHARED_SCAN, variant)
+    host, ss = star
+    queries = [datagen.ss_query(13, qid) for qid in range(20)]
+    mix = [ss.compile(q) for q in queries]
+    ss.run_shared(mix)
+    for cq, q in zip(mix, queries):
+        alone = ss.compile(q)
+        ss.run(alone)
+        assert torch.equal(alone.sums, cq.sums) and torch.equal(alone.counts, cq.counts)
+        _check(orc, host, cq, q)
+    crys.check_device_errors()
+    crys.crys_set_tile(crys.OP_SHARED_SCAN, 0)
+
+
+def test_shared_scan_segments_accumulate(crys, orc, star):
+    host, ss = star
+    queries = [datagen.ss_query(14, qid) for qid in range(32)]
+    mix = [ss.compile(q) for q in queries]
+    n = ss.n_rows
+    cuts = [0, 4096, 65_536, 65_540, 200_000, n]
+    for i, (a, b) in enumerate(zip(cuts[:-1], cuts[1:])):
+        ss.run_shared(mix, a, b, accumulate=i > 0)
+    for cq, q in zip(mix, queries):
+        _check(orc, host, cq, q)
+
+
+def test_group_accumulator_modes(crys, orc, star):
+    # G = 1 (registers), small G (shared memory) and G = 25 * 1000 * 7 = 175000 groups,
+    # beyond the shared-memory budget (global atomics), must all agree with the oracle.
+    host, ss = star
+    qs = [
+        {"id": 0, "fact_preds": [], "joins": [{"dim": "date", "filters": [], "group": None}],
+         "agg": ("sum", "price", None)},
+        {"id": 1, "fact_preds": [("disc", 1, 3)],
+         "joins": [{"dim": "supp", "filters": [("region", 0, 2)], "group": "nation"},
+                   {"dim": "date", "filters": [], "group": "year"}], "agg": ("mul", "price", "disc")},
+        {"id": 2, "fact_preds": [],
+         "joins": [{"dim": "cust", "filters": [], "group": "nation"},
+                   {"dim": "part", "filters": [("mfgr", 1, 3)], "group": "brand"},
+                   {"dim": "date", "filters": [], "group": "year"}], "agg": ("sub", "price", "cost")},
+    ]
+    for q in qs:
+        cq = ss.compile(q)
+        ss.run(cq)
+        _check(orc, host, cq, q)
+    mix = [ss.compile(q) for q in qs]
+    ss.run_shared(mix)
+    for cq, q in zip(mix, qs):
+        _check(orc, host, cq, q)
