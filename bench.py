@@ -1,0 +1,581 @@
+"""Benchmark of the tile-based query operators on GB300.
+
+Default workload (``--workload served``): the served star-schema stream — a fact table of
+600M rows x 8 int32 columns resident in HBM and four dimensions (2556 / 200K / 3M / 1.4M
+rows); a step is one batch of 32 seeded select-join-group-by queries: their dimension
+hash tables are built (one build kernel per join) and all 32 run in ONE shared scan of
+the fact table.  ``value`` is queries/s over the K timed steps (CUDA events, inputs
+resident, fact table 19.2 GB >> L2).  The JSON line also carries the one-query-at-a-time
+baseline on the same GPU, the served loop (continuous batching through the public API:
+queries in from the host, results back to pinned host memory) with p50/p99 latency, the
+dominant kernel's roofline, the CPU oracle timed on a sample of the same workload, SM
+clocks sampled during the timed region, and the number of library kernels launched.
+
+Other workloads (``--workload select|project|join|sort|q1``) time one operator of the
+hot path each and report GB/s of algorithmic traffic against measured HBM bandwidth.
+
+``--impl reference`` times the oracle (plain CPU code) on the same workload, on the
+host cores, as the reference arm.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "scanned GB/s vs GB300 HBM peak per query; served queries/s, p50/p99 latency"
+BATCH = 32
+FALLBACK_HBM_GBS = 6800.0
+
+
+# ----------------------------------------------------------------------------- helpers
+
+def measured_hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            with open(self.path) as f:
+                for line in f:
+                    parts = [p.strip() for p in line.split(",")]
+                    if len(parts) >= 9 and parts[1].replace(".", "").isdigit():
+                        rows.append(parts)
+        except Exception:
+            pass
+        finally:
+            try:
+                os.unlink(self.path)
+            except Exception:
+                pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in rows]
+        mx = max(float(r[2]) for r in rows)
+        loaded = [s for s in sm if s > 0.5 * mx] or sm
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": mx, "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())
+                if any(r[3].replace(".", "").isdigit() for r in rows) else None}
+
+
+def dist_setup(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if args.impl != "reference" else "gloo")
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class KernelTimer:
+    """CUDA events around launches on one stream; returns per-launch milliseconds."""
+
+    def __init__(self, stream):
+        self.stream = stream
+        self.pairs = []
+
+    def __enter__(self):
+        import torch
+        self.a = torch.cuda.Event(enable_timing=True)
+        self.a.record(self.stream)
+        return self
+
+    def __exit__(self, *exc):
+        import torch
+        b = torch.cuda.Event(enable_timing=True)
+        b.record(self.stream)
+        self.pairs.append((self.a, b))
+
+    def ms(self):
+        return [a.elapsed_time(b) for a, b in self.pairs]
+
+
+def l2_flush(buf):
+    buf.zero_()
+
+
+# ----------------------------------------------------------------------------- served
+
+def served_store(seed, n_rows, dim_scale, device):
+    import datagen.device as dgd
+    from paper_2003_01178_gb300.starschema import ResidentStarSchema, served_schema
+    t = dgd.ss_tables(seed, n_rows, device, dim_scale)
+    return ResidentStarSchema(served_schema(), t["fact"], t["dims"])
+
+
+def batch_queries(seed, step, rank=0):
+    import datagen
+    base = (rank * 100_000) + step * BATCH
+    return [datagen.ss_query(seed, base + i) for i in range(BATCH)]
+
+
+def run_served(args, rank, world, local):
+    import torch
+    import datagen
+    import paper_2003_01178_gb300 as crys
+
+    dev = torch.device("cuda", local)
+    seed = args.seed
+    store = served_store(seed, args.rows, args.dim_scale, dev)
+    stream = torch.cuda.current_stream(dev)
+    torch.cuda.synchronize(dev)
+    peak, peak_kind = measured_hbm_peak()
+
+    def one_step(step, timers=None):
+        qs = batch_queries(seed, step, rank)
+        cqs = [store.compile(q) for q in qs]
+        if timers is not None:
+            with timers:
+                store.run_shared(cqs)
+        else:
+            store.run_shared(cqs)
+        return qs, cqs
+
+    for w in range(args.warmup):
+        one_step(10_000 + w)
+    torch.cuda.synchronize(dev)
+    scan_timer = KernelTimer(stream)
+    launches0 = crys.crys_launch_count()
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clocks:
+        start = torch.cuda.Event(enable_timing=True)
+        end = torch.cuda.Event(enable_timing=True)
+        start.record(stream)
+        step_queries = []
+        for s in range(args.steps):
+            qs, _ = one_step(s, scan_timer)
+            step_queries.append(qs)
+        end.record(stream)
+        torch.cuda.synchronize(dev)
+    barrier(world)
+    launches = crys.crys_launch_count() - launches0
+    elapsed_ms = max_over_ranks(start.elapsed_time(end), world)
+    total_queries = BATCH * args.steps * world
+    qps = total_queries / (elapsed_ms / 1e3)
+    scan_ms = scan_timer.ms()
+    avg_scan_ms = sum(scan_ms) / len(scan_ms)
+    union_cols = len(store.schema.fact_cols)
+    scan_bytes = union_cols * store.n_rows * 4
+    per_query_bytes = [store.bytes_scanned(q) for qs in step_queries for q in qs]
+    scanned_gbs = sum(per_query_bytes) / (elapsed_ms / 1e3) / 1e9 * world
+
+    out = {
+        "metric": METRIC, "value": round(qps, 2), "unit": "queries/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(elapsed_ms / args.steps, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+        "data": "synthetic (seeded counter-based generator, generated in HBM)",
+        "config": {"workload": "served star-schema stream: fact 600M rows x 8 int32 cols (19.2 GB), "
+                               "dims 2556/200K/3M/1.4M rows, batches of 32 seeded select-join-group-by "
+                               "queries (1-4 joins, selectivity 1e-4..0.5, <=1e4 groups, int64 sums)",
+                   "fact_rows": store.n_rows, "batch_queries": BATCH,
+                   "step": "build the batch's dimension hash tables + one shared scan of the fact table",
+                   "l2": "inputs larger than L2 (19.2 GB fact table per scan)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "scanned_gbs": {"aggregate": round(scanned_gbs, 1),
+                        "per_query_mean_gb": round(sum(per_query_bytes) / len(per_query_bytes) / 1e9, 3),
+                        "note": "sum over queries of each query's own column bytes / wall time"},
+        "gpu_launches": int(launches),
+    }
+    achieved = scan_bytes / (avg_scan_ms / 1e3) / 1e9
+    out["roofline"] = {"kernel": "shared_scan_kernel", "bound": "hbm", "achieved": round(achieved, 1),
+                       "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                       "peak_source": peak_kind, "traffic": traffic_for("shared_scan_kernel", args),
+                       "algorithmic_bytes_per_launch": scan_bytes, "avg_launch_ms": round(avg_scan_ms, 4)}
+    # one query at a time on the same GPU, same batches
+    if not args.quick:
+        alone_ms = []
+        for s in range(min(args.steps, 3)):
+            qs = batch_queries(seed, s, rank)
+            torch.cuda.synchronize(dev)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for q in qs:
+                cq = store.compile(q)
+                store.run(cq)
+            b.record(stream)
+            torch.cuda.synchronize(dev)
+            alone_ms.append(a.elapsed_time(b))
+        out["one_at_a_time"] = {"queries_per_s": round(BATCH / (sum(alone_ms) / len(alone_ms) / 1e3), 2),
+                                "note": "same batches, one fused probe kernel per query, same GPU"}
+        out["served"] = served_loop(store, args, rank)
+        out["e2e"] = {"value": out["served"]["closed_loop_qps"], "unit": "queries/s",
+                      "h2d_bytes_per_step": out["served"]["h2d_bytes_per_batch"],
+                      "d2h_bytes_per_step": out["served"]["d2h_bytes_per_batch"],
+                      "what": "public serving API: query dicts in from the host, plans compiled, "
+                              "dimension tables built, circular shared scans, int64 results copied "
+                              "to pinned host memory; fact table resident (the workload's premise)"}
+    out["clocks"] = clocks.summary()
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline_served(store, args)
+    return out
+
+
+def served_loop(store, args, rank):
+    import datagen
+    from paper_2003_01178_gb300.server import QueryServer
+    n = args.served_queries
+    queries = [datagen.ss_query(args.seed, 500_000 + rank * 100_000 + i) for i in range(n)]
+    server = QueryServer(store, segments=args.segments, max_slots=BATCH, memory_budget=16 << 30)
+    # closed loop: every request queued at t=0 (throughput)
+    _, st_closed = server.serve(queries, np.zeros(n), realtime=False)
+    # open loop: Poisson arrivals at 70% of the closed-loop rate (latency)
+    rate = max(1.0, 0.7 * st_closed.qps)
+    arrivals = datagen.ss_arrivals(args.seed, n, rate)
+    _, st_open = server.serve(queries, arrivals, realtime=True)
+    groups = sum(store.groups(q) for q in queries)
+    return {"closed_loop_qps": round(st_closed.qps, 2), "open_loop_offered_qps": round(rate, 2),
+            "open_loop_qps": round(st_open.qps, 2),
+            "p50_ms": round(st_open.percentile_ms(50), 3), "p99_ms": round(st_open.percentile_ms(99), 3),
+            "closed_loop_p50_ms": round(st_closed.percentile_ms(50), 3),
+            "closed_loop_p99_ms": round(st_closed.percentile_ms(99), 3),
+            "queries": n, "segments": args.segments, "max_active": st_open.max_active,
+            "launches": st_open.launches,
+            "h2d_bytes_per_batch": 0,
+            "d2h_bytes_per_batch": int(16 * groups / n * BATCH)}
+
+
+def oracle_threads():
+    import oracle
+    return oracle.hardware_threads()
+
+
+def cpu_baseline_served(store, args):
+    """The oracle (plain row-at-a-time C, rows split over all host threads) on a sample:
+    the first batch's 32 queries over the first `sample_rows` fact rows, scaled to the
+    full table."""
+    import datagen
+    import oracle
+    rows = min(args.cpu_sample_rows, store.n_rows)
+    host = {"fact": {c: store.fact[c][:rows].cpu().numpy() for c in store.schema.fact_cols},
+            "dims": {d: {k: v.cpu().numpy() for k, v in t.items()} for d, t in store.dims.items()}}
+    threads = oracle_threads()
+    qs = batch_queries(args.seed, 0)
+    t0 = time.perf_counter()
+    for q in qs:
+        oracle.ss_run(host, q, threads=threads)
+    dt = time.perf_counter() - t0
+    full_dt = dt * store.n_rows / rows
+    return {"value": round(BATCH / full_dt, 4), "unit": "queries/s", "cores": threads, "kind": "oracle",
+            "sample": f"32 queries of step 0 over the first {rows} of {store.n_rows} fact rows "
+                      f"({dt:.2f} s), scaled by rows"}
+
+
+# ----------------------------------------------------------------------------- operators
+
+def traffic_for(kernel, args):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the
+    current source of the kernel; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    try:
+        src_hash = kernel_source_hash()
+        with open(path) as f:
+            for line in f:
+                parts = line.split()
+                if len(parts) >= 4 and parts[0] == kernel and parts[1] == args.workload and parts[2] == src_hash:
+                    return int(parts[3])
+    except Exception:
+        pass
+    return None
+
+
+def kernel_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2003_01178_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
+def op_line(args, world, name, value, unit, kernel, alg_bytes, avg_ms, config, extra=None):
+    peak, kind = measured_hbm_peak()
+    achieved = alg_bytes / (avg_ms / 1e3) / 1e9
+    out = {"metric": METRIC, "value": round(value, 2), "unit": unit, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(avg_ms, 4),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": config.pop("dtype", "int32"), "data": "synthetic (seeded counter-based generator)",
+           "config": dict(workload=name, **config),
+           "roofline": {"kernel": kernel, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                        "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_source": kind,
+                        "traffic": traffic_for(kernel, args), "algorithmic_bytes_per_launch": int(alg_bytes),
+                        "avg_launch_ms": round(avg_ms, 4)}}
+    if extra:
+        out.update(extra)
+    return out
+
+
+def time_launches(fn, steps, warmup, stream, flush=None):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(steps):
+        if flush is not None:
+            flush()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    return ms
+
+
+def run_operator(args, rank, world, local):
+    import torch
+    import datagen
+    import datagen.device as dgd
+    import paper_2003_01178_gb300 as crys
+
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    seed = args.seed
+    launches0 = crys.crys_launch_count()
+    with ClockSampler(local) as clocks:
+        if args.workload == "select":
+            n = args.rows or (1 << 29)
+            x = dgd.uniform_i32(seed, datagen.STREAMS["sel.x"], n, 0, (1 << 31) - 1, dev)
+            out = torch.empty(n, dtype=torch.int32, device=dev)
+            cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+            sweep = {}
+            for sigma in [i / 10 for i in range(11)]:
+                hi = datagen.select_threshold(sigma)
+                ms = time_launches(lambda: crys.crys_select(x, n, -(1 << 31), hi, out, cnt, 0),
+                                   args.steps, args.warmup, stream)
+                sweep[f"{sigma:.1f}"] = statistics.median(ms)
+            avg = statistics.mean(sweep.values())
+            alg = statistics.mean([4 * n * (1 + float(s)) for s in sweep])
+            line = op_line(args, world, "select", alg / (avg / 1e3) / 1e9, "GB/s", "select_kernel", alg, avg,
+                           {"rows": n, "selectivity": "0.0..1.0 step 0.1 (mean over the sweep)",
+                            "l2": "inputs larger than L2"},
+                           {"sweep_ms": {k: round(v, 4) for k, v in sweep.items()}})
+        elif args.workload == "project":
+            n = args.rows or (1 << 29)
+            x1 = dgd.uniform_f32(seed, datagen.STREAMS["proj.x1"], n, dev)
+            x2 = dgd.uniform_f32(seed, datagen.STREAMS["proj.x2"], n, dev)
+            y = torch.empty_like(x1)
+            res = {}
+            for op, nm in ((crys.PROJ_LINEAR, "linear"), (crys.PROJ_SIGMOID, "sigmoid")):
+                res[nm] = statistics.median(time_launches(
+                    lambda: crys.crys_project(x1, x2, n, 2.0, 3.0, op, y), args.steps, args.warmup, stream))
+            avg = statistics.mean(res.values())
+            line = op_line(args, world, "project", 12 * n / (avg / 1e3) / 1e9, "GB/s", "project_kernel", 12 * n, avg,
+                           {"rows": n, "dtype": "f32", "l2": "inputs larger than L2"},
+                           {"ms": {k: round(v, 4) for k, v in res.items()}})
+        elif args.workload == "join":
+            n_probe = args.rows or (1 << 28)
+            fk_pay = None
+            res = {}
+            for lg in args.join_sizes:
+                nb = 1 << lg
+                bk = dgd.perm_i32(seed, datagen.STREAMS["join.bkey"], nb, dev)
+                bv = dgd.uniform_i32(seed, datagen.STREAMS["join.bval"], nb, 1, 100, dev)
+                ht = crys.HashTable.build(bk, bv)
+                fk = dgd.uniform_i32(seed, datagen.STREAMS["join.fk"], n_probe, 0, nb - 1, dev)
+                pay = dgd.uniform_i32(seed, datagen.STREAMS["join.pay"], n_probe, 1, 100, dev) if fk_pay is None else fk_pay
+                fk_pay = pay
+                s = torch.zeros(2, dtype=torch.int64, device=dev)
+                ms = time_launches(lambda: crys.crys_probe_aggregate(fk, pay, n_probe, ht.struct, s[0:1], s[1:2]),
+                                   args.steps, args.warmup, stream)
+                bms = time_launches(lambda: (crys.crys_hash_init(ht.struct), crys.crys_hash_build(bk, bv, nb, [], ht.struct)),
+                                    max(1, args.steps // 2), 1, stream)
+                res[f"2^{lg}"] = {"probe_ms": round(statistics.median(ms), 4), "build_ms": round(statistics.median(bms), 4),
+                                  "table_mb": round(ht.nbytes / 2 ** 20, 3)}
+                del ht, bk, bv, fk
+            # headline: the largest table (HBM-resident probes)
+            last = res[f"2^{args.join_sizes[-1]}"]
+            alg = 8 * n_probe
+            line = op_line(args, world, "join", alg / (last["probe_ms"] / 1e3) / 1e9, "GB/s", "probe_kernel", alg,
+                           last["probe_ms"], {"probe_rows": n_probe, "build_rows": f"2^{args.join_sizes[0]}..2^{args.join_sizes[-1]}",
+                                              "fill": "50%", "l2": "probe side larger than L2"},
+                           {"sweep": res, "note": "algorithmic bytes = probe scan 8|P| only; slot reads are extra traffic"})
+        elif args.workload == "sort":
+            n = args.rows or (1 << 28)
+            keys = dgd.bits_i32(seed, datagen.STREAMS["sort.key"], n, dev)
+            vals = torch.arange(n, dtype=torch.int32, device=dev)
+            ko, vo = torch.empty_like(keys), torch.empty_like(vals)
+            tb = crys.crys_sort(None, None, None, None, n, None, -1)
+            temp = crys.scratch(tb, dev)
+            ms = time_launches(lambda: crys.crys_sort(keys, vals, ko, vo, n, temp, tb), args.steps, args.warmup, stream)
+            avg = statistics.median(ms)
+            line = op_line(args, world, "sort", n / (avg / 1e3) / 1e6, "Mkeys/s", "sort_pass_kernel", 68 * n, avg,
+                           {"rows": n, "l2": "inputs larger than L2", "passes": "4 x 8-bit, stable"})
+        elif args.workload == "q1":
+            n = args.rows or (1 << 22)
+            t = dgd.q1_tables(seed, n, dev)
+            f, d = t["fact"], t["dim"]
+            ht = crys.HashTable.build(d["key"], d["yr"], filters=[(d["yr"], 3, 3)])
+            sums = torch.zeros(1, dtype=torch.int64, device=dev)
+            cnts = torch.zeros(1, dtype=torch.int64, device=dev)
+            table = crys.make_table([f["fk"], f["a"], f["b"], f["c"]])
+            plan = crys.make_plan([(1, -(1 << 31), 24), (2, 1, 3)], [(0, ht, 0)], ("mul", 3, 2), sums, cnts)
+            flush_buf = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+            ms = time_launches(lambda: crys.crys_run_plan(table, plan), args.steps, args.warmup, stream,
+                               flush=lambda: l2_flush(flush_buf))
+            avg = statistics.median(ms)
+            line = op_line(args, world, "q1", 16 * n / (avg / 1e3) / 1e9, "GB/s", "plan_kernel", 16 * n, avg,
+                           {"rows": n, "dtype": "int64", "l2": "flushed between timed launches (512 MB write)"})
+        else:
+            raise SystemExit(f"unknown workload {args.workload}")
+    line["gpu_launches"] = int(crys.crys_launch_count() - launches0)
+    line["clocks"] = clocks.summary()
+    return line
+
+
+# ----------------------------------------------------------------------------- reference arm
+
+def run_reference(args, rank, world):
+    """The oracle as it stands, on the host cores, on a bounded sample of each step's
+    workload, scaled to the same unit as our arm."""
+    if rank != 0:
+        return None
+    import datagen
+    import oracle
+    oracle.build()
+    threads = oracle.hardware_threads()
+    if args.workload != "served":
+        raise SystemExit("--impl reference is implemented for the served workload")
+    rows = min(args.cpu_sample_rows, args.rows)
+    host = datagen.ss_tables(args.seed, rows, dim_scale=args.dim_scale)
+    times = []
+    for s in range(args.warmup + args.steps):
+        qs = batch_queries(args.seed, s)
+        t0 = time.perf_counter()
+        for q in qs:
+            oracle.ss_run(host, q, threads=threads)
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            times.append(dt * args.rows / rows)
+    total = sum(times)
+    qps = BATCH * args.steps / total
+    return {"metric": METRIC, "value": round(qps, 4), "unit": "queries/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total / args.steps * 1e3, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic (seeded counter-based generator)", "impl": "reference",
+            "config": {"workload": "served star-schema stream (see our arm)", "fact_rows": args.rows,
+                       "batch_queries": BATCH},
+            "cpu_baseline": {"value": round(qps, 4), "unit": "queries/s", "cores": threads, "kind": "oracle",
+                             "sample": f"each step: 32 queries over the first {rows} fact rows, time scaled "
+                                       f"to {args.rows} rows"},
+            "e2e": {"value": round(qps, 4), "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+# ----------------------------------------------------------------------------- main
+
+def main():
+    p = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--workload", default="served", choices=["served", "select", "project", "join", "sort", "q1"])
+    p.add_argument("--rows", type=int, default=None)
+    p.add_argument("--dim-scale", type=float, default=1.0)
+    p.add_argument("--seed", type=int, default=0xC0FFEE + 4)
+    p.add_argument("--segments", type=int, default=8)
+    p.add_argument("--served-queries", type=int, default=512)
+    p.add_argument("--cpu-sample-rows", type=int, default=6_000_000)
+    p.add_argument("--join-sizes", type=int, nargs="+", default=[10, 14, 18, 20, 22, 24, 26, 27])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--quick", action="store_true", help="skip the one-at-a-time and served-loop legs")
+    args = p.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("at least 3 warm-up steps")
+    if args.workload == "served" and args.rows is None:
+        args.rows = 600_000_000
+    rank, world, local = dist_setup(args)
+    if args.impl == "reference":
+        line = run_reference(args, rank, world)
+        if line is not None:
+            print(json.dumps(line), flush=True)
+        return
+    import paper_2003_01178_gb300 as crys
+    crys.lib()
+    if args.workload == "served":
+        line = run_served(args, rank, world, local)
+    else:
+        line = run_operator(args, rank, world, local)
+    crys.check_device_errors()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

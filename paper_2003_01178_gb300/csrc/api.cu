@@ -2,6 +2,7 @@
 // counter, SM counts and the tile-shape choice of each operator.
 #include <atomic>
 #include <mutex>
+#include <unordered_map>
 
 #include "common.cuh"
 #include "tiles.h"
@@ -50,6 +51,20 @@ int sm_count() {
     g_sms[dev] = v > 0 ? v : 1;
   }
   return g_sms[dev];
+}
+
+bool set_dynamic_smem(const void* kernel, size_t bytes) {
+  static std::mutex m;
+  static std::unordered_map<const void*, size_t> done[kMaxDevices];
+  const int dev = current_device();
+  std::lock_guard<std::mutex> lock(m);
+  auto it = done[dev].find(kernel);
+  if (it != done[dev].end() && it->second >= bytes) return true;
+  if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           static_cast<int>(bytes)) != cudaSuccess)
+    return false;
+  done[dev][kernel] = bytes;
+  return true;
 }
 
 int tile_variant(int op) {

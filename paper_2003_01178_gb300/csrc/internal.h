@@ -46,12 +46,15 @@ int persistent_grid(K kernel, int threads, size_t smem, int64_t tiles) {
   return g < 1 ? 1 : static_cast<int>(g);
 }
 
-// Opts a kernel into more than 48 KB of dynamic shared memory (once per process).
+// Opts a kernel into `bytes` of dynamic shared memory.  Without the opt-in, static
+// plus dynamic shared memory of a block is limited to 48 KB, so every kernel that
+// takes dynamic shared memory sets the attribute (once per kernel and size).
+bool set_dynamic_smem(const void* kernel, size_t bytes);
+
 template <typename K>
 bool allow_smem(K kernel, size_t bytes) {
-  if (bytes <= 48 * 1024) return true;
-  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              static_cast<int>(bytes)) == cudaSuccess;
+  if (bytes == 0) return true;
+  return set_dynamic_smem(reinterpret_cast<const void*>(kernel), bytes);
 }
 
 }  // namespace crys
