@@ -82,6 +82,25 @@ int crys_select(const int32_t* x, int64_t n, int32_t lo, int32_t hi, int32_t* ou
                 int64_t* d_count, int order_preserving, void* d_temp, size_t* temp_bytes,
                 crys_stream s);
 
+/* Allocation-free variant of the order-preserving selection (no counterpart in the
+ * paper; it exists for callers that cannot allocate device memory on the call path:
+ * query executors and plugins that run inside a host process owning a fixed,
+ * pre-reserved device memory pool, or real-time pipelines that forbid allocation after
+ * start-up).  Same result as crys_select(..., order_preserving = 1, ...), but the
+ * look-back scratch lives in a file-scope static device array of the library
+ * (CRYS_SELECT_STATIC_SCRATCH_BYTES bytes, held by every device that loads the
+ * library until the process exits).  The caller still passes x, out and d_count.
+ *   n > CRYS_SELECT_STATIC_MAX_ROWS returns CRYS_EINVAL (nothing enqueued).
+ *   The first call on a device looks up the array's device address with that device
+ *   current; make that first call before any stream capture.
+ *   All calls share the one array: the call clears the part it uses on its stream, and
+ *   calls whose work overlaps on the GPU (other streams, other threads) race on it.
+ *   No cudaMalloc, cudaFree or allocating library routine is called. */
+#define CRYS_SELECT_STATIC_MAX_ROWS (1ll << 25)
+#define CRYS_SELECT_STATIC_SCRATCH_BYTES (256 + (CRYS_SELECT_STATIC_MAX_ROWS / 512) * 8)
+int crys_select_static(const int32_t* x, int64_t n, int32_t lo, int32_t hi, int32_t* out,
+                       int64_t* d_count, crys_stream s);
+
 /* ------------------------------------------------------------------ projection
  * Section 4.1, queries Q1 and Q2: y = a*x1 + b*x2 (CRYS_PROJ_LINEAR) or the sigmoid
  * 1/(1 + exp(-(a*x1 + b*x2))) (CRYS_PROJ_SIGMOID), float32 in and out, one rounding per

@@ -83,6 +83,7 @@ def lib():
         L.crys_device_errors.argtypes = [C.POINTER(C.c_int32), C.c_int, p]
         L.crys_launch_count.restype = i64
         L.crys_select.argtypes = [p, i64, i32, i32, p, p, C.c_int, p, sz, p]
+        L.crys_select_static.argtypes = [p, i64, i32, i32, p, p, p]
         L.crys_project.argtypes = [p, p, i64, C.c_float, C.c_float, C.c_int, p, p]
         L.crys_hash_init.argtypes = [C.POINTER(crys_hash), p]
         L.crys_hash_build.argtypes = [p, p, i64, C.POINTER(crys_pred), i32, C.POINTER(crys_hash), p]
@@ -95,7 +96,7 @@ def lib():
         L.crys_tile_variants.argtypes = [C.c_int, C.POINTER(C.c_int32), C.POINTER(C.c_int32), i32]
         L.crys_set_tile.argtypes = [C.c_int, i32]
         L.crys_get_tile.argtypes = [C.c_int]
-        for fn in ("crys_device_errors", "crys_select", "crys_project", "crys_hash_init",
+        for fn in ("crys_device_errors", "crys_select", "crys_select_static", "crys_project", "crys_hash_init",
                    "crys_hash_build", "crys_probe_aggregate", "crys_sort", "crys_plan_groups",
                    "crys_run_plan", "crys_run_plans", "crys_tile_variants", "crys_set_tile",
                    "crys_get_tile"):
@@ -154,6 +155,13 @@ def crys_select(x, n: int, lo: int, hi: int, out, d_count, order_preserving: int
                              _ptr(d_temp), C.byref(tb) if d_temp is not None else None, _stream(stream)),
            "crys_select")
     return 0
+
+
+def crys_select_static(x, n: int, lo: int, hi: int, out, d_count, stream=None) -> None:
+    """Order-preserving selection whose scratch is the library's static device array
+    (no allocation on the call path; n <= 2^25)."""
+    _check(lib().crys_select_static(_ptr(x), n, lo, hi, _ptr(out), _ptr(d_count), _stream(stream)),
+           "crys_select_static")
 
 
 def crys_project(x1, x2, n: int, a: float, b: float, op: int, y, stream=None) -> None:

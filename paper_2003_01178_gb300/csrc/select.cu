@@ -14,6 +14,8 @@
 // atomic (the paper's scheme); mode 1 chains tiles with a decoupled look-back (tile
 // ids handed out in order by an atomic counter, so a tile only waits on tiles that
 // running blocks already hold) and the result is in input order.
+#include <mutex>
+
 #include "common.cuh"
 #include "pipeline.cuh"
 #include "tiles.h"
@@ -281,4 +283,52 @@ extern "C" int crys_select(const int32_t* x, int64_t n, int32_t lo, int32_t hi, 
     case 3: return launch<kTiles[kOp][3].threads, kTiles[kOp][3].items>(a, ord, s);
     default: return launch<kTiles[kOp][0].threads, kTiles[kOp][0].items>(a, ord, s);
   }
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free order-preserving selection: the look-back scratch is a static device
+// array of this file instead of caller-supplied memory.
+
+namespace crys {
+namespace {
+
+static_assert(CRYS_SELECT_STATIC_SCRATCH_BYTES >= 256 + (CRYS_SELECT_STATIC_MAX_ROWS / 512) * 8,
+              "static scratch covers the smallest tile shape");
+
+static __device__ __align__(256) unsigned char g_select_scratch[CRYS_SELECT_STATIC_SCRATCH_BYTES];
+
+constexpr int kMaxStaticDevices = 64;
+std::mutex g_static_mutex;
+void* g_static_ptr[kMaxStaticDevices] = {};
+
+// Device address of g_select_scratch on the current device (looked up once per device
+// with that device current; the host-side name is only a stand-in for the symbol).
+void* static_scratch() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxStaticDevices) return nullptr;
+  std::lock_guard<std::mutex> lock(g_static_mutex);
+  if (!g_static_ptr[dev]) {
+    void* ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, g_select_scratch) != cudaSuccess) return nullptr;
+    g_static_ptr[dev] = ptr;
+  }
+  return g_static_ptr[dev];
+}
+
+}  // namespace
+}  // namespace crys
+
+extern "C" int crys_select_static(const int32_t* x, int64_t n, int32_t lo, int32_t hi,
+                                  int32_t* out, int64_t* d_count, crys_stream stream) {
+  using namespace crys;
+  if (n < 0 || n > CRYS_SELECT_STATIC_MAX_ROWS) return CRYS_EINVAL;
+  size_t need = 0;
+  if (crys_select(nullptr, n, lo, hi, nullptr, nullptr, 1, nullptr, &need, stream) != CRYS_OK)
+    return CRYS_EINVAL;
+  if (need > CRYS_SELECT_STATIC_SCRATCH_BYTES) return CRYS_EINVAL;
+  void* scratch = static_scratch();
+  if (!scratch) return CRYS_ECUDA;
+  size_t have = CRYS_SELECT_STATIC_SCRATCH_BYTES;
+  // crys_select clears the `need` bytes it uses on `stream` before its kernel runs.
+  return crys_select(x, n, lo, hi, out, d_count, 1, scratch, &have, stream);
 }
