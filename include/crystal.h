@@ -160,16 +160,28 @@ int crys_sort(const int32_t* keys_in, const int32_t* vals_in, int32_t* keys_out,
               int32_t* vals_out, int64_t n, void* d_temp, size_t* temp_bytes, crys_stream s);
 
 /* ------------------------------------------------------------------ query plans
- * Section 5.3: a select-join-aggregate query runs as one build kernel per dimension
- * (crys_hash_build with the dimension's filter) and ONE probe kernel over the fact
- * table that, per tile, applies the fact predicates, probes the dimension tables in
- * plan order (rows that miss are dropped), forms the group id from the joined values,
- * and accumulates SUM(expr) and COUNT per group.  Group id g is the mixed-radix number
- * of the grouped joins' values (first grouped join most significant); the number of
- * groups G is the product of their group_card (1 when nothing is grouped). */
+ * Section 5.3: a select-join-aggregate query runs as build kernels for its dimension
+ * tables and ONE probe kernel over the fact table that, per tile, applies the fact
+ * predicates, probes the dimension tables (rows that miss are dropped), checks the
+ * dimension predicates, forms the group id from the joined values, and accumulates
+ * SUM(expr) and COUNT per group.
+ *
+ * A dimension table maps key -> a 32-bit value.  Two ways to use it:
+ *  - the paper's plan: build the table with the dimension filter applied at build time
+ *    (crys_hash_build filters) and the group attribute as the value; the join then has
+ *    no predicates and takes the whole value as its group code;
+ *  - resident tables: build ONE table per dimension whose value packs several
+ *    attribute codes into bit fields (crys_pack_fields); each query then states its
+ *    dimension predicates and its group attribute as bit fields of the value, and all
+ *    queries share the table (no per-query build).
+ * Field (shift, bits) of a value v is (v >> shift) & (2^bits - 1) for 0 < bits < 32 and
+ * the whole int32 v for bits == 0 or 32.  The group id g is the mixed-radix number of
+ * the grouped joins' codes in plan order (first grouped join most significant); the
+ * number of groups G is the product of their group_card (1 when nothing is grouped). */
 #define CRYS_MAX_COLS 16
 #define CRYS_MAX_PREDS 8
 #define CRYS_MAX_JOINS 4
+#define CRYS_MAX_FIELD_PREDS 2
 #define CRYS_MAX_PLANS 32
 
 #define CRYS_AGG_A 0       /* SUM(a) */
@@ -189,9 +201,17 @@ typedef struct {
 } crys_col_pred;
 
 typedef struct {
-  int32_t fk_col;     /* fact column holding the foreign key */
-  crys_hash ht;       /* filtered dimension table: key -> group value */
-  int32_t group_card; /* 0: membership only; else the value is a group code in [0, card) */
+  int32_t shift, bits; /* bit field of the joined value (see above) */
+  int32_t lo, hi;      /* lo <= field <= hi */
+} crys_field_pred;
+
+typedef struct {
+  int32_t fk_col;                 /* fact column holding the foreign key */
+  crys_hash ht;                   /* dimension table: key -> value */
+  int32_t group_card;             /* 0: not grouped; else group code in [0, group_card) */
+  int32_t group_shift, group_bits; /* bit field of the value holding the group code */
+  int32_t n_preds;                /* dimension predicates on bit fields of the value */
+  crys_field_pred preds[CRYS_MAX_FIELD_PREDS];
 } crys_join;
 
 typedef struct {
@@ -207,16 +227,25 @@ typedef struct {
 /* Number of groups G of a plan (product of group_card over grouped joins). */
 int crys_plan_groups(const crys_plan* plan, int64_t* groups);
 
+/* out[i] = OR over k of (cols[k][i] & (2^bits[k] - 1)) << shifts[k], for the dimension
+ * value of a resident table (done once when a dimension is loaded; the paper likewise
+ * dictionary-encodes attributes before loading, Section 5.2).  cols is a HOST array of
+ * n_fields (1..8) device column pointers; fields must not overlap or pass bit 31. */
+int crys_pack_fields(const int32_t* const* cols, const int32_t* shifts, const int32_t* bits,
+                     int32_t n_fields, int64_t n, int32_t* out, crys_stream s);
+
 /* One query over all fact rows; overwrites the plan's outputs. */
 int crys_run_plan(const crys_table* fact, const crys_plan* plan, crys_stream s);
 
 /* Shared scan: up to CRYS_MAX_PLANS queries over rows [row_begin, row_end) of the same
  * fact table in ONE kernel: each tile of the union of the queries' columns is read from
  * HBM once (staged in shared memory by bulk asynchronous copies) and every query is
- * evaluated on it.  With CRYS_ACCUMULATE the outputs are added to instead of
- * overwritten, so a query can be carried across several row segments (a circular
- * scan that queries join and leave at segment boundaries).  row_begin must be a
- * multiple of 4. */
+ * evaluated on it.  When the queries' joins use at most 8 distinct (fact column, table)
+ * pairs, each distinct pair is probed once per row for the whole batch and the queries
+ * read the probed values; otherwise every query probes its own tables.  With
+ * CRYS_ACCUMULATE the outputs are added to instead of overwritten, so a query can be
+ * carried across several row segments (a circular scan that queries join and leave at
+ * segment boundaries).  row_begin must be a multiple of 4. */
 #define CRYS_ACCUMULATE 0x1
 int crys_run_plans(const crys_table* fact, const crys_plan* plans, int32_t n_plans,
                    int64_t row_begin, int64_t row_end, int flags, crys_stream s);

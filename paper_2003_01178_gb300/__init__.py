@@ -25,7 +25,7 @@ DEV_TIMEOUT, DEV_TABLE_FULL, DEV_BAD_KEY, DEV_DUP_KEY, DEV_BAD_GROUP, DEV_BOUNDS
 PROJ_LINEAR, PROJ_SIGMOID = 0, 1
 AGG_A, AGG_A_MUL_B, AGG_A_SUB_B, AGG_A_ADD_B = 0, 1, 2, 3
 AGG_OPS = {"sum": AGG_A, "mul": AGG_A_MUL_B, "sub": AGG_A_SUB_B, "add": AGG_A_ADD_B}
-MAX_COLS, MAX_PREDS, MAX_JOINS, MAX_PLANS = 16, 8, 4, 32
+MAX_COLS, MAX_PREDS, MAX_JOINS, MAX_PLANS, MAX_FIELD_PREDS = 16, 8, 4, 32, 2
 ACCUMULATE = 1
 OP_SELECT, OP_PROJECT, OP_PROBE, OP_PLAN, OP_SHARED_SCAN, OP_SORT = range(6)
 OP_NAMES = ["select", "project", "probe", "plan", "shared_scan", "sort"]
@@ -55,8 +55,14 @@ class crys_col_pred(C.Structure):
     _fields_ = [("col", C.c_int32), ("lo", C.c_int32), ("hi", C.c_int32)]
 
 
+class crys_field_pred(C.Structure):
+    _fields_ = [("shift", C.c_int32), ("bits", C.c_int32), ("lo", C.c_int32), ("hi", C.c_int32)]
+
+
 class crys_join(C.Structure):
-    _fields_ = [("fk_col", C.c_int32), ("ht", crys_hash), ("group_card", C.c_int32)]
+    _fields_ = [("fk_col", C.c_int32), ("ht", crys_hash), ("group_card", C.c_int32),
+                ("group_shift", C.c_int32), ("group_bits", C.c_int32), ("n_preds", C.c_int32),
+                ("preds", crys_field_pred * MAX_FIELD_PREDS)]
 
 
 class crys_plan(C.Structure):
@@ -90,6 +96,8 @@ def lib():
         L.crys_probe_aggregate.argtypes = [p, p, i64, C.POINTER(crys_hash), p, p, p]
         L.crys_sort.argtypes = [p, p, p, p, i64, p, sz, p]
         L.crys_plan_groups.argtypes = [C.POINTER(crys_plan), C.POINTER(C.c_int64)]
+        L.crys_pack_fields.argtypes = [C.POINTER(C.c_void_p), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                       i32, i64, p, p]
         L.crys_run_plan.argtypes = [C.POINTER(crys_table), C.POINTER(crys_plan), p]
         L.crys_run_plans.argtypes = [C.POINTER(crys_table), C.POINTER(crys_plan), i32, i64, i64,
                                      C.c_int, p]
@@ -98,6 +106,7 @@ def lib():
         L.crys_get_tile.argtypes = [C.c_int]
         for fn in ("crys_device_errors", "crys_select", "crys_select_static", "crys_project", "crys_hash_init",
                    "crys_hash_build", "crys_probe_aggregate", "crys_sort", "crys_plan_groups",
+                   "crys_pack_fields",
                    "crys_run_plan", "crys_run_plans", "crys_tile_variants", "crys_set_tile",
                    "crys_get_tile"):
             getattr(L, fn).restype = C.c_int
@@ -199,6 +208,14 @@ def crys_plan_groups(plan: crys_plan) -> int:
     g = C.c_int64(0)
     _check(lib().crys_plan_groups(C.byref(plan), C.byref(g)), "crys_plan_groups")
     return g.value
+
+
+def crys_pack_fields(cols: list, shifts: list, bits: list, n: int, out, stream=None) -> None:
+    k = len(cols)
+    carr = (C.c_void_p * max(1, k))(*[_ptr(c) for c in cols])
+    sarr = (C.c_int32 * max(1, k))(*shifts)
+    barr = (C.c_int32 * max(1, k))(*bits)
+    _check(lib().crys_pack_fields(carr, sarr, barr, k, n, _ptr(out), _stream(stream)), "crys_pack_fields")
 
 
 def crys_run_plan(fact: crys_table, plan: crys_plan, stream=None) -> None:
@@ -333,7 +350,10 @@ def make_table(cols: list) -> crys_table:
 
 
 def make_plan(preds, joins, agg, sums: torch.Tensor, counts: torch.Tensor | None) -> crys_plan:
-    """preds: [(col, lo, hi)]; joins: [(fk_col, HashTable, group_card)]; agg: (op, a, b)."""
+    """preds: [(col, lo, hi)]; joins: [(fk_col, HashTable, group_card)] for tables whose
+    value is the group code, or [(fk_col, HashTable, group_card, (group_shift, group_bits),
+    [(shift, bits, lo, hi), ...])] for tables whose value packs attribute fields;
+    agg: (op, a, b)."""
     p = crys_plan()
     if len(preds) > MAX_PREDS or len(joins) > MAX_JOINS:
         raise ValueError("too many predicates or joins")
@@ -341,8 +361,19 @@ def make_plan(preds, joins, agg, sums: torch.Tensor, counts: torch.Tensor | None
     for i, (c, lo, hi) in enumerate(preds):
         p.preds[i] = crys_col_pred(c, lo, hi)
     p.n_joins = len(joins)
-    for i, (fk, ht, card) in enumerate(joins):
-        p.joins[i] = crys_join(fk, ht.struct, card)
+    for i, jn in enumerate(joins):
+        fk, ht, card = jn[0], jn[1], jn[2]
+        js = crys_join()
+        js.fk_col, js.ht, js.group_card = fk, ht.struct, card
+        if len(jn) > 3:
+            js.group_shift, js.group_bits = jn[3]
+            fps = list(jn[4])
+            if len(fps) > MAX_FIELD_PREDS:
+                raise ValueError("too many dimension predicates")
+            js.n_preds = len(fps)
+            for k, (sh, bi, lo, hi) in enumerate(fps):
+                js.preds[k] = crys_field_pred(sh, bi, lo, hi)
+        p.joins[i] = js
     op, a, b = agg
     p.agg_op = AGG_OPS[op] if isinstance(op, str) else op
     p.agg_a = a
@@ -354,7 +385,8 @@ def make_plan(preds, joins, agg, sums: torch.Tensor, counts: torch.Tensor | None
 
 def plan_groups(joins) -> int:
     g = 1
-    for _, _, card in joins:
+    for jn in joins:
+        card = jn[2]
         if card > 0:
             g *= card
     return g

@@ -1,17 +1,20 @@
 // Fused select-join-aggregate pipelines (Section 5.3; Figure "tile-extension"): after
-// one build kernel per dimension, ONE kernel streams the fact table in tiles and, per
+// the dimension tables are built, ONE kernel streams the fact table in tiles and, per
 // tile, applies the fact predicates (BlockPred), loads later columns only for rows still
 // alive (BlockLoadSel: a 16-byte group is fetched only if one of its rows is alive), probes
-// the dimension tables in plan order (BlockLookup), forms the group id from the joined
-// values and accumulates SUM(expr) and COUNT per group (BlockAggregate into per-block
-// partials, flushed with one atomic per non-empty group and block).
+// the dimension tables (BlockLookup), checks the dimension predicates on bit fields of
+// the joined values, forms the group id and accumulates SUM(expr) and COUNT per group
+// (BlockAggregate into per-block partials, flushed with one atomic per non-empty group
+// and block).
 //
 // Two kernels share the per-query evaluation:
-//  * plan_kernel       one query; columns read straight from global memory so that
-//                      BlockLoadSel saves sectors of dead rows.
+//  * plan_kernel        one query; columns read straight from global memory so that
+//                       BlockLoadSel saves sectors of dead rows.
 //  * shared_scan_kernel up to 32 queries over the same fact table; the union of their
-//                      columns is staged per tile in shared memory by bulk copies, so each
-//                      fact tile crosses HBM once however many queries read it.
+//                       columns is staged per tile in shared memory by bulk copies, so
+//                       each fact tile crosses HBM once however many queries read it,
+//                       and each distinct (foreign key, table) pair of the batch is
+//                       probed once per row for all queries that join through it.
 #include "common.cuh"
 #include "pipeline.cuh"
 #include "tiles.h"
@@ -20,12 +23,19 @@ namespace crys {
 namespace {
 
 enum AccMode : int32_t { kAccSingle = 0, kAccShared = 1, kAccGlobal = 2 };
+constexpr int kMaxProbes = 8;  // distinct (fk column, table) pairs probed once per batch
 
 struct DevJoin {
   const uint64_t* slots;
-  uint32_t mask, shift;
+  uint32_t mask, shift;  // table capacity - 1, hash shift
   int32_t fk_col;
-  int32_t card;  // 0: membership only
+  int32_t card;    // 0: not grouped
+  int32_t stride;  // mixed-radix weight of this join's group code
+  uint32_t gshift, gmask;
+  int32_t n_fp;
+  uint32_t fp_shift[CRYS_MAX_FIELD_PREDS], fp_mask[CRYS_MAX_FIELD_PREDS];
+  int32_t fp_lo[CRYS_MAX_FIELD_PREDS], fp_hi[CRYS_MAX_FIELD_PREDS];
+  int32_t probe;  // index of the batch-wide probe that serves this join, -1: probe here
 };
 
 struct DevQuery {
@@ -42,6 +52,11 @@ struct DevQuery {
   unsigned long long* sums;
   unsigned long long* counts;
 };
+
+// Bit field of a joined value: the whole value when the mask is all ones.
+__device__ __forceinline__ int32_t field_of(int32_t v, uint32_t shift, uint32_t mask) {
+  return static_cast<int32_t>((static_cast<uint32_t>(v) >> shift) & mask);
+}
 
 // Column access from global memory (plan_kernel).  Tiles start at multiples of 4 rows
 // from a 4-row-aligned segment start, so full groups are 16-byte vector loads.
@@ -73,6 +88,13 @@ struct StagedCols {
   }
 };
 
+// Values probed once per batch: value of item i of thread t for probe d at
+// values[(d * ITEMS + i) * THREADS + t]; found bits at found[d * THREADS + t].
+struct Probed {
+  const int32_t* values;
+  const uint32_t* found;
+};
+
 __device__ __forceinline__ void unpack4(int4 q, int32_t* dst) {
   dst[0] = q.x;
   dst[1] = q.y;
@@ -80,22 +102,39 @@ __device__ __forceinline__ void unpack4(int4 q, int32_t* dst) {
   dst[3] = q.w;
 }
 
+// Probes one table for this thread's ITEMS rows: all first-slot reads are issued before
+// any is resolved.  Returns the bitmap of rows whose key was found; values in `value`.
+template <int ITEMS>
+__device__ __forceinline__ uint32_t probe_items(const uint64_t* slots, uint32_t mask, uint32_t shift,
+                                                const int32_t (&key)[ITEMS], uint32_t live,
+                                                int32_t (&value)[ITEMS], uint64_t pol) {
+  uint32_t h[ITEMS];
+  uint64_t slot[ITEMS];
+#pragma unroll
+  for (int i = 0; i < ITEMS; ++i) {
+    h[i] = hash_slot(key[i], shift);
+    slot[i] = ((live >> i) & 1u) ? ld_slot(slots + h[i], pol) : kEmptySlot;
+  }
+  uint32_t found = 0;
+#pragma unroll
+  for (int i = 0; i < ITEMS; ++i) {
+    value[i] = 0;
+    if (((live >> i) & 1u) && hash_resolve(slots, mask, h[i], slot[i], key[i], &value[i], pol))
+      found |= 1u << i;
+  }
+  return found;
+}
+
 // Evaluates one query on this thread's ITEMS rows of a tile (4-row groups
 // j*THREADS + tid).  Returns the bitmap of rows that qualify; gid/val hold their group
 // id and aggregate value.
 template <int THREADS, int ITEMS, typename Cols>
-__device__ __forceinline__ uint32_t eval_query(const DevQuery& q, const Cols& cols, int valid,
-                                               int32_t (&gid)[ITEMS], int64_t (&val)[ITEMS],
-                                               int32_t* err, uint64_t pol_table) {
+__device__ __forceinline__ uint32_t eval_query(const DevQuery& q, const Cols& cols, uint32_t alive,
+                                               const Probed& probed, int32_t (&gid)[ITEMS],
+                                               int64_t (&val)[ITEMS], int32_t* err,
+                                               uint64_t pol_table) {
   constexpr int VEC = ITEMS / 4;
   const int tid = threadIdx.x;
-  uint32_t alive = 0;
-#pragma unroll
-  for (int j = 0; j < VEC; ++j) {
-    const int p = (j * THREADS + tid) * 4;
-#pragma unroll
-    for (int e = 0; e < 4; ++e) alive |= static_cast<uint32_t>(p + e < valid) << (4 * j + e);
-  }
   // BlockPred over the fact predicates, each column read only for live groups.
   for (int f = 0; f < q.n_preds && alive; ++f) {
     const int c = q.pred_col[f];
@@ -113,37 +152,44 @@ __device__ __forceinline__ uint32_t eval_query(const DevQuery& q, const Cols& co
   }
 #pragma unroll
   for (int i = 0; i < ITEMS; ++i) gid[i] = 0;
-  // BlockLookup into each dimension table, in plan order.
+  // BlockLookup into each dimension table (or read the batch-wide probe results).
   for (int jn = 0; jn < q.n_joins && alive; ++jn) {
     const DevJoin& J = q.joins[jn];
-    int32_t key[ITEMS];
+    int32_t value[ITEMS];
+    if (J.probe >= 0) {
+      alive &= probed.found[J.probe * THREADS + tid];
 #pragma unroll
-    for (int j = 0; j < VEC; ++j) {
-      if ((alive >> (4 * j)) & 0xFu)
-        unpack4(cols.load4(J.fk_col, (j * THREADS + tid) * 4), key + 4 * j);
-      else
-        key[4 * j] = key[4 * j + 1] = key[4 * j + 2] = key[4 * j + 3] = 0;
+      for (int i = 0; i < ITEMS; ++i) value[i] = probed.values[(J.probe * ITEMS + i) * THREADS + tid];
+    } else {
+      int32_t key[ITEMS];
+#pragma unroll
+      for (int j = 0; j < VEC; ++j) {
+        if ((alive >> (4 * j)) & 0xFu)
+          unpack4(cols.load4(J.fk_col, (j * THREADS + tid) * 4), key + 4 * j);
+        else
+          key[4 * j] = key[4 * j + 1] = key[4 * j + 2] = key[4 * j + 3] = 0;
+      }
+      alive &= probe_items<ITEMS>(J.slots, J.mask, J.shift, key, alive, value, pol_table);
     }
-    uint32_t h[ITEMS];
-    uint64_t slot[ITEMS];
+    for (int f = 0; f < J.n_fp; ++f) {
+      const uint32_t sh = J.fp_shift[f], mk = J.fp_mask[f];
+      const int32_t lo = J.fp_lo[f], hi = J.fp_hi[f];
 #pragma unroll
-    for (int i = 0; i < ITEMS; ++i) {
-      h[i] = hash_slot(key[i], J.shift);
-      slot[i] = ((alive >> i) & 1u) ? ld_slot(J.slots + h[i], pol_table) : kEmptySlot;
+      for (int i = 0; i < ITEMS; ++i) {
+        const int32_t fv = field_of(value[i], sh, mk);
+        if (fv < lo || fv > hi) alive &= ~(1u << i);
+      }
     }
+    if (J.card > 0) {
+      const uint32_t card = static_cast<uint32_t>(J.card);
 #pragma unroll
-    for (int i = 0; i < ITEMS; ++i) {
-      if (!((alive >> i) & 1u)) continue;
-      int32_t value;
-      if (!hash_resolve(J.slots, J.mask, h[i], slot[i], key[i], &value, pol_table)) {
-        alive &= ~(1u << i);
-      } else if (J.card > 0) {
-        if (static_cast<uint32_t>(value) >= static_cast<uint32_t>(J.card)) {
+      for (int i = 0; i < ITEMS; ++i) {
+        const uint32_t code = static_cast<uint32_t>(field_of(value[i], J.gshift, J.gmask));
+        if (((alive >> i) & 1u) && code >= card) {
           set_error(err, CRYS_DEV_BAD_GROUP);
           alive &= ~(1u << i);
-        } else {
-          gid[i] = gid[i] * J.card + value;
         }
+        gid[i] += static_cast<int32_t>(code) * J.stride;
       }
     }
   }
@@ -170,6 +216,20 @@ __device__ __forceinline__ uint32_t eval_query(const DevQuery& q, const Cols& co
     }
   }
   return alive;
+}
+
+// Rows of this thread that exist in a tile with `valid` rows.
+template <int THREADS, int ITEMS>
+__device__ __forceinline__ uint32_t rows_present(int valid) {
+  constexpr int VEC = ITEMS / 4;
+  uint32_t live = 0;
+#pragma unroll
+  for (int j = 0; j < VEC; ++j) {
+    const int p = (j * THREADS + static_cast<int>(threadIdx.x)) * 4;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) live |= static_cast<uint32_t>(p + e < valid) << (4 * j + e);
+  }
+  return live;
 }
 
 // Accumulator shared memory of a block: sums (8 B) then counts (4 B) per group.
@@ -225,6 +285,7 @@ __global__ void __launch_bounds__(THREADS) plan_kernel(const __grid_constant__ P
   uint64_t my_sum = 0, my_count = 0;
   const uint64_t pol = policy_evict_first();
   const uint64_t pol_table = policy_evict_last();
+  const Probed none = {nullptr, nullptr};
   for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     GlobalCols cols;
     cols.pol = pol;
@@ -233,7 +294,8 @@ __global__ void __launch_bounds__(THREADS) plan_kernel(const __grid_constant__ P
     cols.valid = static_cast<int>((nrows - t * TILE) < TILE ? (nrows - t * TILE) : TILE);
     int32_t gid[ITEMS];
     int64_t val[ITEMS];
-    const uint32_t alive = eval_query<THREADS, ITEMS>(q, cols, cols.valid, gid, val, a.err, pol_table);
+    const uint32_t alive = eval_query<THREADS, ITEMS>(q, cols, rows_present<THREADS, ITEMS>(cols.valid),
+                                                      none, gid, val, a.err, pol_table);
     if (!alive) continue;
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
@@ -267,6 +329,12 @@ __global__ void __launch_bounds__(THREADS) plan_kernel(const __grid_constant__ P
 
 constexpr int kScanMaxStages = 3;
 
+struct ProbeSpec {
+  const uint64_t* slots;
+  uint32_t mask, shift;
+  int32_t fk_col;
+};
+
 struct ScanArgs {
   const int32_t* cols[CRYS_MAX_COLS];
   int32_t slot_of[CRYS_MAX_COLS];     // table column -> staged slice, -1 if unused
@@ -275,21 +343,28 @@ struct ScanArgs {
   int32_t stages;
   int64_t row_begin, row_end;
   int32_t n_queries;
+  int32_t n_probes;       // batch-wide probes (0: every join probes for its own query)
   int32_t shared_groups;  // accumulators held in shared memory, all queries
   int32_t* err;
+  ProbeSpec probes[kMaxProbes];
   DevQuery q[CRYS_MAX_PLANS];
 };
 
 template <int THREADS, int ITEMS>
 __global__ void __launch_bounds__(THREADS) shared_scan_kernel(const __grid_constant__ ScanArgs a) {
   constexpr int TILE = THREADS * ITEMS;
+  constexpr int VEC = ITEMS / 4;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ StageRing<kScanMaxStages> ring;
   const int S = a.stages;
   const int tid = threadIdx.x, lane = tid % kWarp;
+  // dynamic shared memory: stages | probed values | probed found bits | accumulators
   int32_t* stages = reinterpret_cast<int32_t*>(smem_raw);
   const size_t stage_elems = static_cast<size_t>(a.n_union) * TILE;
-  const SharedAcc acc = shared_acc(smem_raw + S * stage_elems * sizeof(int32_t), a.shared_groups);
+  int32_t* pvalues = stages + S * stage_elems;
+  uint32_t* pfound = reinterpret_cast<uint32_t*>(pvalues + static_cast<size_t>(a.n_probes) * TILE);
+  const SharedAcc acc = shared_acc(reinterpret_cast<unsigned char*>(pfound + a.n_probes * THREADS),
+                                   a.shared_groups);
   for (int g = tid; g < a.shared_groups; g += THREADS) {
     acc.sums[g] = 0;
     acc.counts[g] = 0;
@@ -328,6 +403,7 @@ __global__ void __launch_bounds__(THREADS) shared_scan_kernel(const __grid_const
     for (int s = 0; s < S; ++s) issue(s);
   __syncthreads();
 
+  const Probed probed = {pvalues, pfound};
   bool aborted = false;
   for (int64_t k = 0;; ++k) {
     const int s = static_cast<int>(k % S);
@@ -354,11 +430,23 @@ __global__ void __launch_bounds__(THREADS) shared_scan_kernel(const __grid_const
     cols.row0 = a.row_begin + t * TILE;
     cols.valid = static_cast<int>((nrows - t * TILE) < TILE ? (nrows - t * TILE) : TILE);
     cols.bulk = cols.valid & ~3;
+    const uint32_t live = rows_present<THREADS, ITEMS>(cols.valid);
+    // Batch-wide BlockLookup: each distinct (fk column, table) pair once per row.  Each
+    // thread keeps the results of its own rows, so no barrier is needed before use.
+    for (int d = 0; d < a.n_probes; ++d) {
+      const ProbeSpec& P = a.probes[d];
+      int32_t key[ITEMS], value[ITEMS];
+#pragma unroll
+      for (int j = 0; j < VEC; ++j) unpack4(cols.load4(P.fk_col, (j * THREADS + tid) * 4), key + 4 * j);
+      pfound[d * THREADS + tid] = probe_items<ITEMS>(P.slots, P.mask, P.shift, key, live, value, pol_table);
+#pragma unroll
+      for (int i = 0; i < ITEMS; ++i) pvalues[(d * ITEMS + i) * THREADS + tid] = value[i];
+    }
     for (int qi = 0; qi < a.n_queries; ++qi) {
       const DevQuery& q = a.q[qi];
       int32_t gid[ITEMS];
       int64_t val[ITEMS];
-      const uint32_t alive = eval_query<THREADS, ITEMS>(q, cols, cols.valid, gid, val, a.err, pol_table);
+      const uint32_t alive = eval_query<THREADS, ITEMS>(q, cols, live, probed, gid, val, a.err, pol_table);
       if (q.acc_mode == kAccSingle) {
         uint64_t s_sum = 0, s_cnt = 0;
 #pragma unroll
@@ -402,10 +490,40 @@ __global__ void __launch_bounds__(THREADS) shared_scan_kernel(const __grid_const
   }
 }
 
+// ------------------------------------------------------------------ packing
+
+struct PackArgs {
+  const int32_t* cols[8];
+  uint32_t shift[8], mask[8];
+  int32_t n_fields;
+  int64_t n;
+  int32_t* out;
+};
+
+__global__ void __launch_bounds__(256) pack_kernel(const __grid_constant__ PackArgs a) {
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < a.n; i += stride) {
+    uint32_t v = 0;
+    for (int k = 0; k < a.n_fields; ++k)
+      v |= (static_cast<uint32_t>(a.cols[k][i]) & a.mask[k]) << a.shift[k];
+    a.out[i] = static_cast<int32_t>(v);
+  }
+}
+
 // ------------------------------------------------------------------ host side
 
 constexpr int64_t kMaxGroups = 1ll << 28;
 constexpr size_t kSharedBudget = 200 * 1024;  // dynamic shared memory a block may use
+
+uint32_t field_mask(int32_t bits) {
+  return (bits <= 0 || bits >= 32) ? 0xFFFFFFFFu : ((1u << bits) - 1u);
+}
+
+bool field_ok(int32_t shift, int32_t bits) {
+  if (bits < 0 || bits > 32 || shift < 0 || shift > 31) return false;
+  if (bits == 0 || bits == 32) return shift == 0;
+  return shift + bits <= 32;
+}
 
 int groups_of(const crys_plan& p, int64_t* groups) {
   if (p.n_joins < 0 || p.n_joins > CRYS_MAX_JOINS) return CRYS_EINVAL;
@@ -439,16 +557,37 @@ int to_device(const crys_table& t, const crys_plan& p, DevQuery* d, uint32_t* co
     mask |= 1u << p.preds[f].col;
   }
   d->n_joins = p.n_joins;
+  // mixed-radix weights: first grouped join most significant
+  int64_t weight = groups;
   for (int j = 0; j < p.n_joins; ++j) {
     const crys_join& J = p.joins[j];
+    DevJoin& D = d->joins[j];
     if (!col_ok(J.fk_col) || !J.ht.slots || !is_pow2(J.ht.capacity) || J.ht.capacity < 2 ||
         J.ht.capacity > (1ll << 31))
       return CRYS_EINVAL;
-    d->joins[j].slots = J.ht.slots;
-    d->joins[j].mask = static_cast<uint32_t>(J.ht.capacity - 1);
-    d->joins[j].shift = 32u - log2_pow2(static_cast<uint64_t>(J.ht.capacity));
-    d->joins[j].fk_col = J.fk_col;
-    d->joins[j].card = J.group_card;
+    if (!field_ok(J.group_shift, J.group_bits) || J.n_preds < 0 || J.n_preds > CRYS_MAX_FIELD_PREDS)
+      return CRYS_EINVAL;
+    D.slots = J.ht.slots;
+    D.mask = static_cast<uint32_t>(J.ht.capacity - 1);
+    D.shift = 32u - log2_pow2(static_cast<uint64_t>(J.ht.capacity));
+    D.fk_col = J.fk_col;
+    D.card = J.group_card;
+    D.stride = 0;
+    if (J.group_card > 0) {
+      weight /= J.group_card;
+      D.stride = static_cast<int32_t>(weight);
+    }
+    D.gshift = static_cast<uint32_t>(J.group_shift);
+    D.gmask = field_mask(J.group_bits);
+    D.n_fp = J.n_preds;
+    for (int f = 0; f < J.n_preds; ++f) {
+      if (!field_ok(J.preds[f].shift, J.preds[f].bits)) return CRYS_EINVAL;
+      D.fp_shift[f] = static_cast<uint32_t>(J.preds[f].shift);
+      D.fp_mask[f] = field_mask(J.preds[f].bits);
+      D.fp_lo[f] = J.preds[f].lo;
+      D.fp_hi[f] = J.preds[f].hi;
+    }
+    D.probe = -1;
     mask |= 1u << J.fk_col;
   }
   if (!col_ok(p.agg_a)) return CRYS_EINVAL;
@@ -512,12 +651,24 @@ template <int THREADS, int ITEMS>
 int launch_scan(ScanArgs& a, cudaStream_t s) {
   constexpr int TILE = THREADS * ITEMS;
   const size_t stage_bytes = static_cast<size_t>(a.n_union) * TILE * sizeof(int32_t);
-  // Shared-memory accumulators for as many queries as fit next to two stages; the rest
-  // accumulate with global atomics.  Single-group queries always take one slot.
-  const size_t budget = kSharedBudget > 2 * stage_bytes ? kSharedBudget - 2 * stage_bytes : 0;
+  const size_t probe_bytes = static_cast<size_t>(a.n_probes) * (TILE + THREADS) * sizeof(int32_t);
+  // Shared-memory accumulators for as many queries as fit next to two stages and the
+  // probe results; the rest accumulate with global atomics.
+  const size_t fixed = 2 * stage_bytes + probe_bytes;
+  const size_t budget = kSharedBudget > fixed ? kSharedBudget - fixed : 0;
+  // Smallest group counts first: they have the most rows per group, where global
+  // atomics would contend most.
+  int order[CRYS_MAX_PLANS];
+  for (int qi = 0; qi < a.n_queries; ++qi) order[qi] = qi;
+  for (int i = 1; i < a.n_queries; ++i)
+    for (int j = i; j > 0 && a.q[order[j]].groups < a.q[order[j - 1]].groups; --j) {
+      const int t = order[j];
+      order[j] = order[j - 1];
+      order[j - 1] = t;
+    }
   int64_t used = 0;
-  for (int qi = 0; qi < a.n_queries; ++qi) {
-    DevQuery& q = a.q[qi];
+  for (int oi = 0; oi < a.n_queries; ++oi) {
+    DevQuery& q = a.q[order[oi]];
     if (static_cast<size_t>(used + q.groups) * 12 <= budget) {
       q.acc_mode = q.groups == 1 ? kAccSingle : kAccShared;
       q.acc_off = static_cast<int32_t>(used);
@@ -528,8 +679,8 @@ int launch_scan(ScanArgs& a, cudaStream_t s) {
   }
   a.shared_groups = static_cast<int32_t>(used);
   const size_t acc_bytes = static_cast<size_t>(used) * 12;
-  a.stages = (3 * stage_bytes + acc_bytes <= kSharedBudget) ? 3 : 2;
-  const size_t smem = a.stages * stage_bytes + acc_bytes;
+  a.stages = (3 * stage_bytes + probe_bytes + acc_bytes <= kSharedBudget) ? 3 : 2;
+  const size_t smem = a.stages * stage_bytes + probe_bytes + acc_bytes;
   if (smem > 227 * 1024) return CRYS_EINVAL;
   auto k = shared_scan_kernel<THREADS, ITEMS>;
   if (!allow_smem(k, smem)) return CRYS_ECUDA;
@@ -541,6 +692,36 @@ int launch_scan(ScanArgs& a, cudaStream_t s) {
   return check_launch();
 }
 
+// Assigns each join of the batch to a batch-wide probe when the batch uses at most
+// kMaxProbes distinct (fk column, table) pairs; otherwise every join probes for its own
+// query.
+void assign_probes(ScanArgs& a) {
+  a.n_probes = 0;
+  ProbeSpec specs[kMaxProbes];
+  int n = 0;
+  auto same = [](const ProbeSpec& p, const DevJoin& J) {
+    return p.slots == J.slots && p.fk_col == J.fk_col && p.mask == J.mask;
+  };
+  for (int qi = 0; qi < a.n_queries; ++qi) {
+    for (int j = 0; j < a.q[qi].n_joins; ++j) {
+      const DevJoin& J = a.q[qi].joins[j];
+      bool known = false;
+      for (int d = 0; d < n; ++d) known = known || same(specs[d], J);
+      if (!known) {
+        if (n == kMaxProbes) return;
+        specs[n] = {J.slots, J.mask, J.shift, J.fk_col};
+        ++n;
+      }
+    }
+  }
+  for (int d = 0; d < n; ++d) a.probes[d] = specs[d];
+  for (int qi = 0; qi < a.n_queries; ++qi)
+    for (int j = 0; j < a.q[qi].n_joins; ++j)
+      for (int d = 0; d < n; ++d)
+        if (same(specs[d], a.q[qi].joins[j])) a.q[qi].joins[j].probe = d;
+  a.n_probes = n;
+}
+
 }  // namespace
 }  // namespace crys
 
@@ -549,6 +730,35 @@ extern "C" {
 int crys_plan_groups(const crys_plan* plan, int64_t* groups) {
   if (!plan || !groups) return CRYS_EINVAL;
   return crys::groups_of(*plan, groups);
+}
+
+int crys_pack_fields(const int32_t* const* cols, const int32_t* shifts, const int32_t* bits,
+                     int32_t n_fields, int64_t n, int32_t* out, crys_stream stream) {
+  using namespace crys;
+  if (n < 0 || n_fields < 1 || n_fields > 8 || !cols || !shifts || !bits) return CRYS_EINVAL;
+  PackArgs a;
+  uint64_t used = 0;
+  for (int k = 0; k < n_fields; ++k) {
+    if (bits[k] < 1 || bits[k] > 31 || shifts[k] < 0 || shifts[k] + bits[k] > 31) return CRYS_EINVAL;
+    const uint64_t m = ((1ull << bits[k]) - 1) << shifts[k];
+    if (used & m) return CRYS_EINVAL;
+    used |= m;
+    if (n > 0 && !cols[k]) return CRYS_EINVAL;
+    a.cols[k] = cols[k];
+    a.shift[k] = static_cast<uint32_t>(shifts[k]);
+    a.mask[k] = (1u << bits[k]) - 1u;
+  }
+  if (n == 0) return CRYS_OK;
+  if (!out) return CRYS_EINVAL;
+  a.n_fields = n_fields;
+  a.n = n;
+  a.out = out;
+  int64_t g = (n + 255) / 256;
+  const int64_t cap = static_cast<int64_t>(sm_count()) * 16;
+  if (g > cap) g = cap;
+  pack_kernel<<<static_cast<unsigned int>(g), 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(a);
+  note_launch();
+  return check_launch();
 }
 
 int crys_run_plan(const crys_table* fact, const crys_plan* plan, crys_stream stream) {
@@ -603,6 +813,7 @@ int crys_run_plans(const crys_table* fact, const crys_plan* plans, int32_t n_pla
       a->union_cols[a->n_union++] = c;
     }
   }
+  assign_probes(*a);
   a->row_begin = row_begin;
   a->row_end = row_end;
   a->err = device_error_word();

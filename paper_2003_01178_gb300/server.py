@@ -60,10 +60,12 @@ class ServeStats:
 
 class QueryServer:
     def __init__(self, store: ResidentStarSchema, segments: int = 8, max_slots: int = MAX_PLANS,
-                 memory_budget: int = 8 << 30, stream: torch.cuda.Stream | None = None):
+                 memory_budget: int = 8 << 30, stream: torch.cuda.Stream | None = None,
+                 mode: str = "resident"):
         if not 1 <= max_slots <= MAX_PLANS:
             raise ValueError("max_slots must be in 1..32")
         self.store = store
+        self.mode = mode
         self.max_slots = max_slots
         self.memory_budget = memory_budget
         self.stream = stream or torch.cuda.Stream(device=store.device)
@@ -80,7 +82,7 @@ class QueryServer:
 
     def _admit(self, req: Request, now: float) -> None:
         with torch.cuda.stream(self.stream):
-            req.compiled = self.store.compile(req.query, stream=self.stream)
+            req.compiled = self.store.compile(req.query, mode=self.mode, stream=self.stream)
         req.admitted_s = now
         req.seen = 0
 
@@ -101,7 +103,7 @@ class QueryServer:
         (footprint above the whole budget) raises MemoryError before anything runs."""
         reqs = [Request(q, float(a) if realtime else 0.0) for q, a in zip(queries, arrivals_s)]
         for r in reqs:
-            r.mem = self.store.memory_needed(r.query)
+            r.mem = self.store.memory_needed(r.query, self.mode)
             if r.mem > self.memory_budget:
                 raise MemoryError(f"query {r.query.get('id')} needs {r.mem} B > budget "
                                   f"{self.memory_budget} B")
@@ -177,9 +179,10 @@ class QueryServer:
 
 
 def one_at_a_time(store: ResidentStarSchema, queries: list, arrivals_s, realtime: bool = True,
-                  stream=None):
+                  stream=None, mode: str = "filtered"):
     """Baseline: FIFO, each query compiled and scanned alone (one fused probe kernel over
-    all fact rows).  Returns (results, stats)."""
+    all fact rows; by default the paper's plan with per-query filtered builds).  Returns
+    (results, stats)."""
     stream = stream or torch.cuda.Stream(device=store.device)
     order = np.argsort(np.asarray(arrivals_s, dtype=np.float64), kind="stable")
     stats = ServeStats()
@@ -191,7 +194,7 @@ def one_at_a_time(store: ResidentStarSchema, queries: list, arrivals_s, realtime
         while realtime and time.perf_counter() - t0 < arrival:
             time.sleep(min(0.001, arrival - (time.perf_counter() - t0)))
         with torch.cuda.stream(stream):
-            cq = store.compile(queries[i], stream=stream)
+            cq = store.compile(queries[i], mode=mode, stream=stream)
             store.run(cq, stream=stream)
             s = torch.empty(cq.groups, dtype=torch.int64, pin_memory=True)
             c = torch.empty(cq.groups, dtype=torch.int64, pin_memory=True)

@@ -1,13 +1,20 @@
 """Select-join-group-by queries over a star schema resident in HBM (Section 5.3).
 
 A query (plain dict: fact predicates, joins with dimension filters and an optional
-group attribute per dimension, one SUM expression) is compiled into the paper's plan
-shape: one build kernel per joined dimension (the dimension filter applied at build
-time, the group attribute as the table's value) and one fused probe kernel over the
-fact table.  Queries over the same fact table can also share one scan
-(``crys_run_plans``).  Hash tables are sized from the filter's expected selectivity
-with a large safety margin; the build flags a full table on the device and
-``check_device_errors`` raises, so a wrong estimate can never go unnoticed.
+group attribute per dimension, one SUM expression) compiles to one of two plan shapes:
+
+* ``mode="filtered"`` — the paper's plan: one build kernel per joined dimension with the
+  dimension filter applied at build time and the group attribute as the table value,
+  then one fused probe kernel over the fact table.  Tables are sized from the filter's
+  expected selectivity with an 8-sigma margin; a full table is flagged on the device and
+  ``check_device_errors`` raises, so a wrong estimate never goes unnoticed.
+* ``mode="resident"`` — every dimension has one resident table, built when the schema is
+  loaded, whose value packs all of the dimension's attribute codes into bit fields; a
+  query's dimension filters and group attribute become bit-field predicates and a
+  bit-field group code on that shared table, so a query needs no build at all and a
+  shared scan probes each dimension once per row for the whole batch.
+
+Both shapes give identical results (integer sums and counts per group).
 """
 from __future__ import annotations
 
@@ -16,8 +23,8 @@ from dataclasses import dataclass, field
 
 import torch
 
-from . import (HashTable, crys_hash_build, crys_hash_init, crys_run_plan, crys_run_plans,
-               make_plan, make_table, capacity_for, ACCUMULATE, MAX_PLANS)
+from . import (HashTable, crys_hash_build, crys_hash_init, crys_pack_fields, crys_run_plan,
+               crys_run_plans, make_plan, make_table, capacity_for, ACCUMULATE, MAX_PLANS)
 
 
 @dataclass
@@ -33,7 +40,7 @@ class CompiledQuery:
     plan: object                       # crys_plan
     sums: torch.Tensor
     counts: torch.Tensor
-    tables: list = field(default_factory=list)   # HashTables kept alive with the plan
+    tables: list = field(default_factory=list)   # per-query HashTables kept alive with the plan
     groups: int = 1
 
     @property
@@ -46,9 +53,9 @@ class CompiledQuery:
 
 
 class ResidentStarSchema:
-    """Fact and dimension columns kept resident on one device."""
+    """Fact and dimension columns (and the packed dimension tables) resident on one device."""
 
-    def __init__(self, schema: Schema, fact: dict, dims: dict):
+    def __init__(self, schema: Schema, fact: dict, dims: dict, stream=None):
         self.schema = schema
         self.fact = fact
         self.dims = dims
@@ -56,6 +63,30 @@ class ResidentStarSchema:
         self.table = make_table(self.cols)
         self.n_rows = self.cols[0].numel()
         self.device = self.cols[0].device
+        self.fields = {}     # dim -> {attr: (shift, bits)}
+        self.resident = {}   # dim -> HashTable(key -> packed attribute codes)
+        self.packed = {}
+        for d, spec in schema.dims.items():
+            shift, fields = 0, {}
+            for attr, card in spec["attrs"].items():
+                bits = max(1, int(card - 1).bit_length())
+                fields[attr] = (shift, bits)
+                shift += bits
+            if shift > 31:
+                raise ValueError(f"attributes of {d} need {shift} bits")
+            dim = dims[d]
+            rows = dim["key"].numel()
+            names = list(fields)
+            packed = torch.empty(rows, dtype=torch.int32, device=self.device)
+            crys_pack_fields([dim[a] for a in names], [fields[a][0] for a in names],
+                             [fields[a][1] for a in names], rows, packed, stream)
+            self.fields[d] = fields
+            self.packed[d] = packed
+            self.resident[d] = HashTable.build(dim["key"], packed, stream=stream)
+
+    @property
+    def resident_bytes(self) -> int:
+        return sum(t.nbytes for t in self.resident.values())
 
     # -- sizing -------------------------------------------------------------------
     def expected_rows(self, join: dict) -> float:
@@ -72,11 +103,6 @@ class ResidentStarSchema:
         rows = self.dims[join["dim"]]["key"].numel()
         return capacity_for(int(min(rows, bound)))
 
-    def memory_needed(self, query: dict) -> int:
-        """Device bytes a query holds while admitted: its hash tables and outputs."""
-        tb = sum(8 * self.table_capacity(j) for j in query["joins"])
-        return tb + 16 * self.groups(query)
-
     def groups(self, query: dict) -> int:
         g = 1
         for j in query["joins"]:
@@ -84,23 +110,38 @@ class ResidentStarSchema:
                 g *= self.schema.dims[j["dim"]]["attrs"][j["group"]]
         return g
 
+    def memory_needed(self, query: dict, mode: str = "resident") -> int:
+        """Device bytes a query holds while admitted: its own hash tables (none with the
+        resident tables) and its outputs (sums and counts, 16 B per group)."""
+        tb = 0 if mode == "resident" else sum(8 * self.table_capacity(j) for j in query["joins"])
+        return tb + 16 * self.groups(query)
+
     # -- compilation ----------------------------------------------------------------
-    def compile(self, query: dict, stream=None) -> CompiledQuery:
+    def compile(self, query: dict, mode: str = "resident", stream=None) -> CompiledQuery:
         names = self.schema.fact_cols
         preds = [(names.index(c), lo, hi) for (c, lo, hi) in query["fact_preds"]]
         joins, tables = [], []
         for j in query["joins"]:
             d = j["dim"]
-            dim = self.dims[d]
             spec = self.schema.dims[d]
-            ht = HashTable(self.table_capacity(j), self.device)
-            crys_hash_init(ht.struct, stream)
-            filters = [(dim[a], lo, hi) for (a, lo, hi) in j["filters"]]
-            vals = dim[j["group"]] if j["group"] is not None else None
-            crys_hash_build(dim["key"], vals, dim["key"].numel(), filters, ht.struct, stream)
+            fk = names.index(spec["fk"])
             card = spec["attrs"][j["group"]] if j["group"] is not None else 0
-            joins.append((names.index(spec["fk"]), ht, card))
-            tables.append(ht)
+            if mode == "resident":
+                fields = self.fields[d]
+                gfield = fields[j["group"]] if j["group"] is not None else (0, 0)
+                fpreds = [(fields[a][0], fields[a][1], lo, hi) for (a, lo, hi) in j["filters"]]
+                joins.append((fk, self.resident[d], card, gfield, fpreds))
+            elif mode == "filtered":
+                dim = self.dims[d]
+                ht = HashTable(self.table_capacity(j), self.device)
+                crys_hash_init(ht.struct, stream)
+                filters = [(dim[a], lo, hi) for (a, lo, hi) in j["filters"]]
+                vals = dim[j["group"]] if j["group"] is not None else None
+                crys_hash_build(dim["key"], vals, dim["key"].numel(), filters, ht.struct, stream)
+                joins.append((fk, ht, card))
+                tables.append(ht)
+            else:
+                raise ValueError(f"unknown mode {mode}")
         op, a, b = query["agg"]
         agg = (op, names.index(a), names.index(b) if b is not None else None)
         g = self.groups(query)
@@ -123,15 +164,18 @@ class ResidentStarSchema:
         crys_run_plans(self.table, [c.plan for c in cqs], row_begin, row_end,
                        ACCUMULATE if accumulate else 0, stream)
 
-    def bytes_scanned(self, query: dict) -> int:
-        """Algorithmic bytes of one query: each fact column it reads, once (4 B/row)."""
+    def query_columns(self, query: dict) -> set:
         cols = {c for (c, _, _) in query["fact_preds"]}
         cols |= {self.schema.dims[j["dim"]]["fk"] for j in query["joins"]}
         op, a, b = query["agg"]
         cols.add(a)
         if b is not None:
             cols.add(b)
-        return 4 * self.n_rows * len(cols)
+        return cols
+
+    def bytes_scanned(self, query: dict) -> int:
+        """Algorithmic bytes of one query: each fact column it reads, once (4 B/row)."""
+        return 4 * self.n_rows * len(self.query_columns(query))
 
 
 def served_schema() -> Schema:

@@ -76,28 +76,32 @@ def _check(orc, host, cq, query):
     assert np.array_equal(cq.counts.cpu().numpy(), rc), query
 
 
+@pytest.mark.parametrize("mode", ["filtered", "resident"])
 @pytest.mark.parametrize("variant", range(4))
-def test_star_queries_one_at_a_time(crys, orc, star, variant):
+def test_star_queries_one_at_a_time(crys, orc, star, variant, mode):
     crys.crys_set_tile(crys.OP_PLAN, variant)
     host, ss = star
     for qid in range(12):
         q = datagen.ss_query(9, qid + 100 * variant)
-        cq = ss.compile(q)
+        cq = ss.compile(q, mode=mode)
         ss.run(cq)
         _check(orc, host, cq, q)
     crys.check_device_errors()
     crys.crys_set_tile(crys.OP_PLAN, 0)
 
 
+@pytest.mark.parametrize("mode", ["filtered", "resident"])
 @pytest.mark.parametrize("variant", range(4))
-def test_shared_scan_equals_alone(crys, orc, star, variant):
+def test_shared_scan_equals_alone(crys, orc, star, variant, mode):
+    # resident mode: one batch-wide probe per dimension; filtered mode: more than 8
+    # distinct tables, so every join probes for its own query
     crys.crys_set_tile(crys.OP_SHARED_SCAN, variant)
     host, ss = star
     queries = [datagen.ss_query(13, qid) for qid in range(20)]
-    mix = [ss.compile(q) for q in queries]
+    mix = [ss.compile(q, mode=mode) for q in queries]
     ss.run_shared(mix)
     for cq, q in zip(mix, queries):
-        alone = ss.compile(q)
+        alone = ss.compile(q, mode="filtered")
         ss.run(alone)
         assert torch.equal(alone.sums, cq.sums) and torch.equal(alone.counts, cq.counts)
         _check(orc, host, cq, q)
@@ -105,10 +109,21 @@ def test_shared_scan_equals_alone(crys, orc, star, variant):
     crys.crys_set_tile(crys.OP_SHARED_SCAN, 0)
 
 
+def test_packed_fields(crys):
+    n = 100_003
+    a = torch.from_numpy(datagen.uniform_i32(1, 1, n, 0, 6)).cuda()
+    b = torch.from_numpy(datagen.uniform_i32(1, 2, n, 0, 999)).cuda()
+    out = torch.empty(n, dtype=torch.int32, device="cuda")
+    crys.crys_pack_fields([a, b], [0, 3], [3, 10], n, out)
+    assert torch.equal(out, a | (b << 3))
+    with pytest.raises(crys.CrystalError):
+        crys.crys_pack_fields([a, b], [0, 2], [3, 10], n, out)   # overlapping fields
+
+
 def test_shared_scan_segments_accumulate(crys, orc, star):
     host, ss = star
     queries = [datagen.ss_query(14, qid) for qid in range(32)]
-    mix = [ss.compile(q) for q in queries]
+    mix = [ss.compile(q, mode="resident") for q in queries]
     n = ss.n_rows
     cuts = [0, 4096, 65_536, 65_540, 200_000, n]
     for i, (a, b) in enumerate(zip(cuts[:-1], cuts[1:])):
@@ -132,11 +147,12 @@ def test_group_accumulator_modes(crys, orc, star):
                    {"dim": "part", "filters": [("mfgr", 1, 3)], "group": "brand"},
                    {"dim": "date", "filters": [], "group": "year"}], "agg": ("sub", "price", "cost")},
     ]
-    for q in qs:
-        cq = ss.compile(q)
-        ss.run(cq)
-        _check(orc, host, cq, q)
-    mix = [ss.compile(q) for q in qs]
-    ss.run_shared(mix)
-    for cq, q in zip(mix, qs):
-        _check(orc, host, cq, q)
+    for mode in ("filtered", "resident"):
+        for q in qs:
+            cq = ss.compile(q, mode=mode)
+            ss.run(cq)
+            _check(orc, host, cq, q)
+        mix = [ss.compile(q, mode=mode) for q in qs]
+        ss.run_shared(mix)
+        for cq, q in zip(mix, qs):
+            _check(orc, host, cq, q)

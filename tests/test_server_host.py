@@ -13,13 +13,14 @@ class FakeStore:
         self.device = torch.device("cpu")
         self._need = need
 
-    def memory_needed(self, query):
+    def memory_needed(self, query, mode="resident"):
         return self._need[query["id"]]
 
 
 def _server(store, **kw):
     s = QueryServer.__new__(QueryServer)
     s.store, s.max_slots, s.memory_budget = store, kw.get("max_slots", 32), kw.get("budget", 1000)
+    s.mode = "resident"
     n = store.n_rows
     step = -(-n // kw.get("segments", 8))
     step = (step + 4095) // 4096 * 4096
