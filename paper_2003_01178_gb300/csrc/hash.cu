@@ -12,7 +12,6 @@
 namespace crys {
 namespace {
 
-constexpr int kStages = 3;
 constexpr int kMaxBuildFilters = 4;
 
 __global__ void fill_empty_kernel(uint64_t* slots, int64_t n) {
@@ -80,6 +79,7 @@ struct ProbeArgs {
   unsigned long long* sum;
   unsigned long long* matches;
   int32_t* err;
+  int32_t stages;
 };
 
 template <int THREADS, int ITEMS>
@@ -88,8 +88,9 @@ __global__ void __launch_bounds__(THREADS) probe_kernel(ProbeArgs a) {
   constexpr int VEC = ITEMS / 4;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   int32_t* stages = reinterpret_cast<int32_t*>(smem_raw);  // per stage: fk tile, payload tile
-  __shared__ StageRing<kStages> ring;
+  __shared__ StageRing ring;
   __shared__ uint64_t red[THREADS / kWarp];
+  const int S = a.stages;
 
   const int tid = threadIdx.x;
   const int64_t ntiles = (a.n + TILE - 1) / TILE;
@@ -112,18 +113,18 @@ __global__ void __launch_bounds__(THREADS) probe_kernel(ProbeArgs a) {
     ring_issue(&ring.full[s], stages + s * 2 * TILE, TILE, cols, 2, row, valid, pol);
   };
 
-  ring_init(ring);
+  ring_init(ring, S);
   if (tid == 0)
-    for (int s = 0; s < kStages; ++s) issue(s);
+    for (int s = 0; s < S; ++s) issue(s);
   __syncthreads();
 
   bool aborted = false;
   for (int64_t k = 0;; ++k) {
-    const int s = static_cast<int>(k % kStages);
+    const int s = static_cast<int>(k % S);
     const int64_t t = ring.tile[s];
     if (t < 0) break;
-    if (!ring_wait(ring, k, a.err)) {
-      if (tid == 0) ring_drain(ring, k, a.err);
+    if (!ring_wait(ring, k, S, a.err)) {
+      if (tid == 0) ring_drain(ring, k, S, a.err);
       aborted = true;
       break;
     }
@@ -177,9 +178,12 @@ __global__ void __launch_bounds__(THREADS) probe_kernel(ProbeArgs a) {
 }
 
 template <int THREADS, int ITEMS>
-int launch_probe(const ProbeArgs& a, cudaStream_t s) {
+int launch_probe(ProbeArgs a, cudaStream_t s) {
   constexpr int TILE = THREADS * ITEMS;
-  const size_t smem = static_cast<size_t>(kStages) * 2 * TILE * sizeof(int32_t);
+  // Probes need warps more than deep staging, and a small table wants L1 left over:
+  // two stages per block.
+  a.stages = 2;
+  const size_t smem = static_cast<size_t>(a.stages) * 2 * TILE * sizeof(int32_t);
   const int64_t ntiles = (a.n + TILE - 1) / TILE;
   auto k = probe_kernel<THREADS, ITEMS>;
   if (!allow_smem(k, smem)) return CRYS_ECUDA;

@@ -32,6 +32,18 @@ inline uint32_t log2_pow2(uint64_t v) {
 
 inline bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
 
+// Number of shared-memory stages for a streaming kernel: as many as fit in a block's
+// share of the SM's shared memory when `blocks_per_sm` blocks are resident, between 2
+// and 8 (the more tiles in flight per SM, the closer a scan gets to HBM bandwidth).
+inline int stages_for(size_t stage_bytes, size_t extra_bytes, int blocks_per_sm) {
+  const size_t per_block = (220u * 1024u) / static_cast<size_t>(blocks_per_sm > 0 ? blocks_per_sm : 1);
+  const size_t room = per_block > extra_bytes ? per_block - extra_bytes : 0;
+  size_t s = room / (stage_bytes > 0 ? stage_bytes : 1);
+  if (s < 2) s = 2;
+  if (s > 8) s = 8;
+  return static_cast<int>(s);
+}
+
 // Persistent grid: resident blocks per SM (from the occupancy calculator) x SMs,
 // capped by the number of tiles.
 template <typename K>

@@ -14,16 +14,17 @@
 
 namespace crys {
 
-template <int S>
+constexpr int kMaxStages = 8;
+
+// The number of stages S (2..kMaxStages) is chosen per launch by the host so that a
+// block's stages fill its share of shared memory.
 struct StageRing {
-  uint64_t full[S];  // completion barrier of each stage (1 arrival + tx bytes)
-  int64_t tile[S];   // tile held by each stage, -1 when none was issued
+  uint64_t full[kMaxStages];  // completion barrier of each stage (1 arrival + tx bytes)
+  int64_t tile[kMaxStages];   // tile held by each stage, -1 when none was issued
 };
 
-template <int S>
-__device__ __forceinline__ void ring_init(StageRing<S>& r) {
+__device__ __forceinline__ void ring_init(StageRing& r, int S) {
   if (threadIdx.x == 0) {
-#pragma unroll
     for (int s = 0; s < S; ++s) {
       mbar_init(&r.full[s], 1);
       r.tile[s] = -1;
@@ -49,16 +50,14 @@ __device__ __forceinline__ void ring_issue(uint64_t* bar, int32_t* stage, int co
 
 // All threads: waits for the stage of local iteration k.  Returns false in every thread
 // when any thread's wait ran out.
-template <int S>
-__device__ __forceinline__ bool ring_wait(StageRing<S>& r, int64_t k, int32_t* err) {
+__device__ __forceinline__ bool ring_wait(StageRing& r, int64_t k, int S, int32_t* err) {
   const bool ok = mbar_wait_bounded(&r.full[k % S], static_cast<uint32_t>((k / S) & 1), err);
   return !__syncthreads_or(!ok);
 }
 
 // Thread 0 after an abandoned iteration k: waits (bounded) for the copies of the
 // iterations k .. k+S-1 that were issued, so no copy lands after the block exits.
-template <int S>
-__device__ __forceinline__ void ring_drain(StageRing<S>& r, int64_t k, int32_t* err) {
+__device__ __forceinline__ void ring_drain(StageRing& r, int64_t k, int S, int32_t* err) {
   for (int j = 0; j < S; ++j) {
     const int64_t kk = k + j;
     const int s = static_cast<int>(kk % S);

@@ -327,8 +327,6 @@ __global__ void __launch_bounds__(THREADS) plan_kernel(const __grid_constant__ P
 
 // ------------------------------------------------------------------ shared scan
 
-constexpr int kScanMaxStages = 3;
-
 struct ProbeSpec {
   const uint64_t* slots;
   uint32_t mask, shift;
@@ -355,7 +353,7 @@ __global__ void __launch_bounds__(THREADS) shared_scan_kernel(const __grid_const
   constexpr int TILE = THREADS * ITEMS;
   constexpr int VEC = ITEMS / 4;
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  __shared__ StageRing<kScanMaxStages> ring;
+  __shared__ StageRing ring;
   const int S = a.stages;
   const int tid = threadIdx.x, lane = tid % kWarp;
   // dynamic shared memory: stages | probed values | probed found bits | accumulators
@@ -679,7 +677,11 @@ int launch_scan(ScanArgs& a, cudaStream_t s) {
   }
   a.shared_groups = static_cast<int32_t>(used);
   const size_t acc_bytes = static_cast<size_t>(used) * 12;
-  a.stages = (3 * stage_bytes + probe_bytes + acc_bytes <= kSharedBudget) ? 3 : 2;
+  {
+    const size_t room = kSharedBudget - probe_bytes - acc_bytes;  // >= 2 stages by construction
+    size_t st = room / (stage_bytes > 0 ? stage_bytes : 1);
+    a.stages = static_cast<int32_t>(st < 2 ? 2 : (st > kMaxStages ? kMaxStages : st));
+  }
   const size_t smem = a.stages * stage_bytes + probe_bytes + acc_bytes;
   if (smem > 227 * 1024) return CRYS_EINVAL;
   auto k = shared_scan_kernel<THREADS, ITEMS>;
@@ -692,12 +694,16 @@ int launch_scan(ScanArgs& a, cudaStream_t s) {
   return check_launch();
 }
 
-// Assigns each join of the batch to a batch-wide probe when the batch uses at most
-// kMaxProbes distinct (fk column, table) pairs; otherwise every join probes for its own
-// query.
+// Assigns batch-wide probes: a (fk column, table) pair joined by two or more queries of
+// the batch is probed once per row for all of them (up to kMaxProbes pairs, most used
+// first); a pair only one query joins is probed by that query itself, after its own
+// predicates have removed rows.
 void assign_probes(ScanArgs& a) {
-  a.n_probes = 0;
-  ProbeSpec specs[kMaxProbes];
+  struct Pair {
+    ProbeSpec spec;
+    int uses;
+  };
+  Pair pairs[CRYS_MAX_PLANS * CRYS_MAX_JOINS];
   int n = 0;
   auto same = [](const ProbeSpec& p, const DevJoin& J) {
     return p.slots == J.slots && p.fk_col == J.fk_col && p.mask == J.mask;
@@ -705,21 +711,34 @@ void assign_probes(ScanArgs& a) {
   for (int qi = 0; qi < a.n_queries; ++qi) {
     for (int j = 0; j < a.q[qi].n_joins; ++j) {
       const DevJoin& J = a.q[qi].joins[j];
-      bool known = false;
-      for (int d = 0; d < n; ++d) known = known || same(specs[d], J);
-      if (!known) {
-        if (n == kMaxProbes) return;
-        specs[n] = {J.slots, J.mask, J.shift, J.fk_col};
-        ++n;
+      int found = -1;
+      for (int d = 0; d < n && found < 0; ++d)
+        if (same(pairs[d].spec, J)) found = d;
+      if (found < 0) {
+        pairs[n].spec = {J.slots, J.mask, J.shift, J.fk_col};
+        pairs[n].uses = 0;
+        found = n++;
       }
+      pairs[found].uses += 1;
     }
   }
-  for (int d = 0; d < n; ++d) a.probes[d] = specs[d];
+  // most used first (stable insertion sort; n <= 128)
+  for (int i = 1; i < n; ++i)
+    for (int j = i; j > 0 && pairs[j].uses > pairs[j - 1].uses; --j) {
+      const Pair t = pairs[j];
+      pairs[j] = pairs[j - 1];
+      pairs[j - 1] = t;
+    }
+  int m = 0;
+  while (m < n && m < kMaxProbes && pairs[m].uses >= 2) {
+    a.probes[m] = pairs[m].spec;
+    ++m;
+  }
   for (int qi = 0; qi < a.n_queries; ++qi)
     for (int j = 0; j < a.q[qi].n_joins; ++j)
-      for (int d = 0; d < n; ++d)
-        if (same(specs[d], a.q[qi].joins[j])) a.q[qi].joins[j].probe = d;
-  a.n_probes = n;
+      for (int d = 0; d < m; ++d)
+        if (same(a.probes[d], a.q[qi].joins[j])) a.q[qi].joins[j].probe = d;
+  a.n_probes = m;
 }
 
 }  // namespace

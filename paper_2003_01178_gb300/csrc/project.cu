@@ -9,7 +9,6 @@
 namespace crys {
 namespace {
 
-constexpr int kStages = 3;
 
 struct ProjectArgs {
   const float* x1;
@@ -18,6 +17,7 @@ struct ProjectArgs {
   float a, b;
   float* y;
   int32_t* err;
+  int32_t stages;
 };
 
 template <int OP>
@@ -41,7 +41,8 @@ __global__ void __launch_bounds__(THREADS) project_kernel(ProjectArgs a) {
   static_assert(ITEMS % 4 == 0, "items per thread must be a multiple of 4");
   extern __shared__ __align__(128) unsigned char smem_raw[];
   int32_t* stages = reinterpret_cast<int32_t*>(smem_raw);  // per stage: x1 tile, x2 tile
-  __shared__ StageRing<kStages> ring;
+  __shared__ StageRing ring;
+  const int S = a.stages;
 
   const int tid = threadIdx.x;
   const int64_t ntiles = (a.n + TILE - 1) / TILE;
@@ -63,17 +64,17 @@ __global__ void __launch_bounds__(THREADS) project_kernel(ProjectArgs a) {
     ring_issue(&ring.full[s], stages + s * 2 * TILE, TILE, cols, 2, row, valid, pol);
   };
 
-  ring_init(ring);
+  ring_init(ring, S);
   if (tid == 0)
-    for (int s = 0; s < kStages; ++s) issue(s);
+    for (int s = 0; s < S; ++s) issue(s);
   __syncthreads();
 
   for (int64_t k = 0;; ++k) {
-    const int s = static_cast<int>(k % kStages);
+    const int s = static_cast<int>(k % S);
     const int64_t t = ring.tile[s];
     if (t < 0) break;
-    if (!ring_wait(ring, k, a.err)) {
-      if (tid == 0) ring_drain(ring, k, a.err);
+    if (!ring_wait(ring, k, S, a.err)) {
+      if (tid == 0) ring_drain(ring, k, S, a.err);
       return;
     }
     const int32_t* st1 = stages + s * 2 * TILE;
@@ -109,9 +110,11 @@ __global__ void __launch_bounds__(THREADS) project_kernel(ProjectArgs a) {
 }
 
 template <int THREADS, int ITEMS>
-int launch(const ProjectArgs& a, int op, cudaStream_t s) {
+int launch(ProjectArgs a, int op, cudaStream_t s) {
   constexpr int TILE = THREADS * ITEMS;
-  const size_t smem = static_cast<size_t>(kStages) * 2 * TILE * sizeof(int32_t);
+  const size_t stage_bytes = static_cast<size_t>(2) * TILE * sizeof(int32_t);
+  a.stages = stages_for(stage_bytes, 1024, THREADS >= 512 ? 1 : 2);
+  const size_t smem = static_cast<size_t>(a.stages) * stage_bytes;
   const int64_t ntiles = (a.n + TILE - 1) / TILE;
   if (op == CRYS_PROJ_SIGMOID) {
     auto k = project_kernel<THREADS, ITEMS, CRYS_PROJ_SIGMOID>;

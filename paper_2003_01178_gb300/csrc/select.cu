@@ -1,14 +1,16 @@
 // Selection (Section 3.2 query Q0, Section 4.2 query Q3) as one persistent kernel.
 //
 // Per tile: BlockLoad (bulk copy into a shared-memory stage) -> BlockPred (range
-// predicate into a per-thread bitmap in registers) -> BlockScan (warp scans of packed
-// per-thread counts, then one warp scans the per-warp segment totals) -> one output
-// reservation per tile -> BlockShuffle (compaction in place in the stage) ->
-// BlockStore (coalesced stores of the compacted run).
+// predicate into a per-thread bitmap in registers) -> BlockScan (a warp scan of packed
+// per-thread counts, then one warp scans the warps' totals) -> one output reservation
+// per tile -> BlockShuffle (each warp compacts its rows into its own shared-memory
+// run) -> BlockStore (coalesced stores of each warp's run).
 //
-// Each thread reads 4-value groups j*THREADS + tid (j < ITEMS/4) of the tile, so a
-// warp's group j is 128 consecutive rows; segments (j, warp) are therefore in input
-// order and the compacted tile keeps input order.
+// Each warp owns a contiguous run of ITEMS*32 rows of the tile (lane l reads the
+// 4-value groups j*128 + 4l, j < ITEMS/4), compacts its selected values in input order
+// into its own shared-memory run, and after one block barrier (warp totals -> offsets
+// and the tile's single output reservation) stores that run with coalesced writes; the
+// stage is handed back to the copy engine right after the first barrier.
 //
 // Output reservation: mode 0 adds the tile's count to the global cursor with one
 // atomic (the paper's scheme); mode 1 chains tiles with a decoupled look-back (tile
@@ -23,7 +25,6 @@
 namespace crys {
 namespace {
 
-constexpr int kStages = 3;
 constexpr uint64_t kFlagAggregate = 1ull << 62;
 constexpr uint64_t kFlagInclusive = 2ull << 62;
 constexpr uint64_t kValueMask = (1ull << 62) - 1;
@@ -32,11 +33,13 @@ struct SelectArgs {
   const int32_t* x;
   int64_t n;
   int32_t lo, hi;
+  uint32_t span;  // hi - lo; only used when lo <= hi
   int32_t* out;
   unsigned long long* count;  // cursor (mode 0) / final count (mode 1)
   uint64_t* tile_state;       // mode 1: one status word per tile
   unsigned int* tile_counter; // mode 1: next tile id
   int32_t* err;
+  int32_t stages;
 };
 
 // Decoupled look-back over tiles 0..t-1 (thread 0 only).  Returns the number of
@@ -80,16 +83,21 @@ __global__ void __launch_bounds__(THREADS) select_kernel(SelectArgs a) {
   constexpr int TILE = THREADS * ITEMS;
   constexpr int VEC = ITEMS / 4;
   constexpr int WARPS = THREADS / kWarp;
-  constexpr int NSEG = VEC * WARPS;
+  constexpr int WROWS = ITEMS * kWarp;  // rows of a tile owned by one warp, contiguous
   static_assert(ITEMS % 4 == 0 && VEC <= 4, "4..16 items per thread");
+  static_assert(WARPS <= kWarp, "one warp scans the warp totals");
 
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  int32_t* stages = reinterpret_cast<int32_t*>(smem_raw);
-  __shared__ StageRing<kStages> ring;
-  __shared__ int32_t seg[NSEG + 1];
+  const int S = a.stages;
+  int32_t* stages = reinterpret_cast<int32_t*>(smem_raw);    // S x TILE
+  int32_t* wbuf_all = stages + S * TILE;                     // per-warp compaction runs
+  __shared__ StageRing ring;
+  __shared__ int32_t wtot[WARPS];
+  __shared__ int32_t woff[WARPS];
   __shared__ long long out_base;
 
   const int tid = threadIdx.x, lane = tid % kWarp, warp = tid / kWarp;
+  int32_t* wbuf = wbuf_all + warp * WROWS;
   const int64_t ntiles = (a.n + TILE - 1) / TILE;
   const uint64_t pol = policy_evict_first();
   int64_t issued = 0;  // thread 0 only
@@ -108,30 +116,31 @@ __global__ void __launch_bounds__(THREADS) select_kernel(SelectArgs a) {
     ring_issue(&ring.full[s], stages + s * TILE, TILE, &a.x, 1, row, valid, pol);
   };
 
-  ring_init(ring);
+  ring_init(ring, S);
   if (tid == 0)
-    for (int s = 0; s < kStages; ++s) issue(s);
+    for (int s = 0; s < S; ++s) issue(s);
   __syncthreads();
 
   for (int64_t k = 0;; ++k) {
-    const int s = static_cast<int>(k % kStages);
+    const int s = static_cast<int>(k % S);
     const int64_t t = ring.tile[s];
     if (t < 0) break;
-    if (!ring_wait(ring, k, a.err)) {
-      if (tid == 0) ring_drain(ring, k, a.err);
+    if (!ring_wait(ring, k, S, a.err)) {
+      if (tid == 0) ring_drain(ring, k, S, a.err);
       return;
     }
-    int32_t* st = stages + s * TILE;
+    const int32_t* st = stages + s * TILE;
     const int64_t row0 = t * TILE;
     const int valid = static_cast<int>((a.n - row0) < TILE ? (a.n - row0) : TILE);
     const int bulk = valid & ~3;
 
-    // BlockLoad + BlockPred: values and bitmap in registers.
+    // BlockLoad + BlockPred: this warp's rows warp*WROWS + j*128 + lane*4 + e, values and
+    // bitmap in registers.
     int32_t v[ITEMS];
     uint32_t bits = 0;
 #pragma unroll
     for (int j = 0; j < VEC; ++j) {
-      const int p = (j * THREADS + tid) * 4;
+      const int p = warp * WROWS + j * 128 + lane * 4;
       const int4 q = stage_read4(st, a.x + row0, p, bulk, valid);
       v[4 * j + 0] = q.x;
       v[4 * j + 1] = q.y;
@@ -139,80 +148,77 @@ __global__ void __launch_bounds__(THREADS) select_kernel(SelectArgs a) {
       v[4 * j + 3] = q.w;
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
-        const bool hit = (p + e < valid) && v[4 * j + e] >= a.lo && v[4 * j + e] <= a.hi;
+        // lo <= v <= hi as one unsigned comparison (span = hi - lo, lo <= hi)
+        const bool hit = (p + e < valid) &&
+                         static_cast<uint32_t>(v[4 * j + e]) - static_cast<uint32_t>(a.lo) <= a.span;
         bits |= static_cast<uint32_t>(hit) << (4 * j + e);
       }
     }
-    // BlockScan, level 1: one warp scan of the per-thread counts of all VEC groups at
-    // once (group j's count in byte j; a warp's group total is at most 128).
+    // BlockScan inside the warp: one scan of the per-lane counts of all VEC groups at
+    // once (group j's count in byte j; a group's warp total is at most 128).
     uint32_t packed = 0;
 #pragma unroll
     for (int j = 0; j < VEC; ++j) packed |= static_cast<uint32_t>(__popc((bits >> (4 * j)) & 0xFu)) << (8 * j);
     const uint32_t incl = static_cast<uint32_t>(warp_inclusive_scan(static_cast<int32_t>(packed), lane));
     const uint32_t excl = incl - packed;
-    if (lane == kWarp - 1) {
+    const uint32_t totals = __shfl_sync(0xFFFFFFFFu, incl, kWarp - 1);
+    // BlockShuffle inside the warp: its selected values, in input order, to its own run.
+    int run = 0;
 #pragma unroll
-      for (int j = 0; j < VEC; ++j) seg[j * WARPS + warp] = static_cast<int32_t>((incl >> (8 * j)) & 0xFFu);
-    }
-    __syncthreads();
-    // Level 2: warp 0 scans the NSEG segment totals (in input order) and reserves the
-    // tile's output range.
-    if (warp == 0) {
-      int32_t carry = 0;
-      for (int c0 = 0; c0 < NSEG; c0 += kWarp) {
-        const int32_t x = (c0 + lane < NSEG) ? seg[c0 + lane] : 0;
-        const int32_t inc = warp_inclusive_scan(x, lane);
-        if (c0 + lane < NSEG) seg[c0 + lane] = carry + inc - x;
-        carry += __shfl_sync(0xFFFFFFFFu, inc, kWarp - 1);
+    for (int j = 0; j < VEC; ++j) {
+      int pos = run + static_cast<int>((excl >> (8 * j)) & 0xFFu);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        if (bits & (1u << (4 * j + e))) wbuf[pos++] = v[4 * j + e];
       }
+      run += static_cast<int>((totals >> (8 * j)) & 0xFFu);
+    }
+    if (lane == 0) wtot[warp] = run;
+    __syncthreads();  // every warp has read the stage and published its count
+    if (warp == 0) {
+      if (lane == 0) {  // the stage is free: refill it now, while the tile is written
+        fence_proxy_async_smem();
+        issue(s);
+      }
+      const int32_t x = lane < WARPS ? wtot[lane] : 0;
+      const int32_t inc = warp_inclusive_scan(x, lane);
+      if (lane < WARPS) woff[lane] = inc - x;
+      const int32_t total = __shfl_sync(0xFFFFFFFFu, inc, kWarp - 1);
       if (lane == 0) {
-        seg[NSEG] = carry;
         long long base;
         if (ORDERED) {
-          base = lookback_exclusive(a.tile_state, t, static_cast<uint64_t>(carry), a.err);
-          if (base >= 0 && t == ntiles - 1) *a.count = static_cast<unsigned long long>(base + carry);
+          base = lookback_exclusive(a.tile_state, t, static_cast<uint64_t>(total), a.err);
+          if (base >= 0 && t == ntiles - 1) *a.count = static_cast<unsigned long long>(base + total);
         } else {
-          base = carry ? static_cast<long long>(atomicAdd(a.count, static_cast<unsigned long long>(carry))) : 0;
+          base = total ? static_cast<long long>(atomicAdd(a.count, static_cast<unsigned long long>(total))) : 0;
+        }
+        if (base >= 0 && base + total > a.n) {
+          set_error(a.err, CRYS_DEV_BOUNDS);
+          base = -1;
         }
         out_base = base;
       }
     }
     __syncthreads();
     const long long base = out_base;
-    const int total = seg[NSEG];
-    if (base < 0) {  // look-back gave up: abandon uniformly
-      if (tid == 0) ring_drain(ring, k, a.err);
+    if (base < 0) {  // look-back gave up (or bounds): abandon uniformly
+      if (tid == 0) ring_drain(ring, k + 1, S, a.err);
       return;
     }
-    // BlockShuffle: compact the selected values in place (every thread already holds
-    // its values in registers, and the scan's barrier ordered all stage reads first).
-#pragma unroll
-    for (int j = 0; j < VEC; ++j) {
-      int pos = seg[j * WARPS + warp] + static_cast<int>((excl >> (8 * j)) & 0xFFu);
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        if (bits & (1u << (4 * j + e))) st[pos++] = v[4 * j + e];
-      }
-    }
-    __syncthreads();
-    // BlockStore: coalesced copy of the compacted run to out[base, base + total).
-    if (base + total <= a.n) {
-      for (int i = tid; i < total; i += THREADS) a.out[base + i] = st[i];
-    } else if (tid == 0) {
-      set_error(a.err, CRYS_DEV_BOUNDS);
-    }
-    __syncthreads();
-    if (tid == 0) {
-      fence_proxy_async_smem();
-      issue(s);
-    }
+    // BlockStore: each warp writes its run with coalesced stores.
+    int32_t* dst = a.out + base + woff[warp];
+    for (int i = lane; i < run; i += kWarp) dst[i] = wbuf[i];
   }
 }
 
 template <int THREADS, int ITEMS>
-int launch(const SelectArgs& a, bool ordered, cudaStream_t s) {
+int launch(SelectArgs a, bool ordered, cudaStream_t s) {
   constexpr int TILE = THREADS * ITEMS;
-  const size_t smem = static_cast<size_t>(kStages) * TILE * sizeof(int32_t);
+  const size_t tile_bytes = static_cast<size_t>(TILE) * sizeof(int32_t);
+  // The select body is issue-bound: keep about 32 warps per SM resident and give each
+  // block the stages that still fit.
+  a.stages = stages_for(tile_bytes, tile_bytes + 1024, (32 * kWarp) / THREADS);
+  const size_t smem = static_cast<size_t>(a.stages + 1) * tile_bytes;
   const int64_t ntiles = (a.n + TILE - 1) / TILE;
   if (ordered) {
     auto k = select_kernel<THREADS, ITEMS, true>;
@@ -260,11 +266,16 @@ extern "C" int crys_select(const int32_t* x, int64_t n, int32_t lo, int32_t hi, 
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (cudaMemsetAsync(d_count, 0, sizeof(int64_t), s) != cudaSuccess) return CRYS_ECUDA;
   if (n == 0) return CRYS_OK;
+  if (lo > hi) {  // empty range: nothing selected (d_count already zeroed)
+    if (order_preserving && cudaMemsetAsync(d_temp, 0, need, s) != cudaSuccess) return CRYS_ECUDA;
+    return CRYS_OK;
+  }
   SelectArgs a;
   a.x = x;
   a.n = n;
   a.lo = lo;
   a.hi = hi;
+  a.span = static_cast<uint32_t>(hi) - static_cast<uint32_t>(lo);
   a.out = out;
   a.count = reinterpret_cast<unsigned long long*>(d_count);
   a.tile_counter = nullptr;

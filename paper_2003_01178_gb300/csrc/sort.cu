@@ -5,9 +5,9 @@
 //  * one up-front kernel reads the keys once and histograms all four digits (the
 //    global start of every digit bucket of every pass, after a 256-wide scan), and
 //  * each pass is ONE kernel: a thread block takes the next tile id from an atomic
-//    counter, ranks its keys stably inside the block (per-warp multisplit with ballots:
-//    keys are processed warp-striped, round by round, so rank order equals input
-//    order), publishes its per-digit counts and finds the counts of all earlier tiles
+//    counter, ranks its keys stably inside the block (per-warp multisplit with
+//    ballots: keys are processed warp-striped, round by round, so rank order equals
+//    input order), publishes its per-digit counts and finds the counts of all earlier tiles
 //    with a decoupled look-back, then writes keys and values through shared memory in
 //    sorted order so that each digit's run is stored with consecutive addresses.
 // So the data crosses HBM once per pass (read 8N, write 8N) plus one 4N key read.
@@ -17,6 +17,7 @@
 // multisplit used here keeps 8-bit stable passes.  Signed order: the top digit has its
 // sign bit flipped.
 #include "common.cuh"
+#include "pipeline.cuh"
 #include "tiles.h"
 
 namespace crys {
@@ -107,48 +108,62 @@ __global__ void __launch_bounds__(THREADS) sort_pass_kernel(PassArgs a) {
   constexpr int WSEG = kWarp * ITEMS;
   static_assert(THREADS >= kRadix, "one thread per digit");
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  int32_t* skeys = reinterpret_cast<int32_t*>(smem_raw);
-  int32_t* svals = skeys + TILE;
+  int32_t* skeys = reinterpret_cast<int32_t*>(smem_raw);  // tile keys: input order, then sorted
+  int32_t* svals = skeys + TILE;                           // tile values: input order, then sorted
   __shared__ unsigned int whist[WARPS][kRadix];  // per-warp digit counts, then offsets
   __shared__ unsigned int tile_start[kRadix];    // tile-local start of each digit run
-  __shared__ long long out_shift[kRadix];        // global position minus local position
+  __shared__ int32_t out_shift[kRadix];          // global position minus local position
   __shared__ unsigned int scan_tmp[kRadix / kWarp];
   __shared__ unsigned int tile_sh;
+  __shared__ __align__(8) uint64_t loaded;
 
   const int tid = threadIdx.x, lane = tid % kWarp, warp = tid / kWarp;
-  const uint64_t pol = policy_evict_first();
-  if (tid == 0) tile_sh = atomicAdd(a.tile_counter, 1u);
+  if (tid == 0) {
+    tile_sh = atomicAdd(a.tile_counter, 1u);
+    mbar_init(&loaded, 1);
+    fence_barrier_init();
+  }
   for (int i = tid; i < WARPS * kRadix; i += THREADS) (&whist[0][0])[i] = 0;
   __syncthreads();
   const int64_t tile = tile_sh;
   const int64_t tile_row = tile * TILE;
-
-  // Load keys and values warp-striped: item i of lane l in warp w is row
-  // tile_row + w*32*ITEMS + i*32 + l.
-  int32_t key[ITEMS], val[ITEMS];
-  uint32_t dig[ITEMS];
-#pragma unroll
-  for (int i = 0; i < ITEMS; ++i) {
-    const int64_t r = tile_row + warp * WSEG + i * kWarp + lane;
-    if (r < a.n) {
-      key[i] = ld_stream(a.keys_in + r, pol);
-      val[i] = ld_stream(a.vals_in + r, pol);
-      dig[i] = digit_of(key[i], a.pass);
-    } else {
-      key[i] = 0;
-      val[i] = 0;
-      dig[i] = kRadix;  // not a row
+  const int valid = static_cast<int>((a.n - tile_row) < TILE ? (a.n - tile_row) : TILE);
+  const int bulk = valid & ~3;
+  // BlockLoad: keys and values of the tile, one bulk copy each.
+  if (tid == 0) {
+    const uint64_t pol = policy_evict_first();
+    const uint32_t bytes = static_cast<uint32_t>(bulk) * 4u;
+    mbar_arrive_expect_tx(&loaded, 2 * bytes);
+    if (bytes) {
+      bulk_load(skeys, a.keys_in + tile_row, bytes, &loaded, pol);
+      bulk_load(svals, a.vals_in + tile_row, bytes, &loaded, pol);
     }
   }
-  // Stable per-warp ranking: in round i the lanes holding the same digit are found
-  // with 8 ballots; each gets (keys of that digit in earlier rounds) + (same-digit
-  // lanes below it).
+  if (bulk < valid) {  // ragged end of the last tile
+    for (int i = bulk + tid; i < valid; i += THREADS) {
+      skeys[i] = a.keys_in[tile_row + i];
+      svals[i] = a.vals_in[tile_row + i];
+    }
+  }
+  const bool ok = mbar_wait_bounded(&loaded, 0, a.err);
+  if (__syncthreads_or(!ok)) {
+    if (tid == 0) mbar_wait_bounded(&loaded, 0, a.err);
+    return;
+  }
+
+  // Stable per-warp ranking, warp-striped: item i of lane l in warp w is tile position
+  // w*32*ITEMS + i*32 + l.  In round i the lanes holding the same digit are found with
+  // 8 ballots (one per digit bit); each gets (keys of that digit in earlier rounds) +
+  // (same-digit lanes below it).  Rows past the end take part in no group.
   const uint32_t lt_mask = (1u << lane) - 1u;
+  int32_t key[ITEMS];
   uint32_t rank[ITEMS];
 #pragma unroll
   for (int i = 0; i < ITEMS; ++i) {
-    const uint32_t d = dig[i];
-    const bool real = d < kRadix;
+    const int pos = warp * WSEG + i * kWarp + lane;
+    const bool real = pos < valid;
+    key[i] = real ? skeys[pos] : 0;
+    const uint32_t d = real ? digit_of(key[i], a.pass) : 0u;
     uint32_t peers = __ballot_sync(0xFFFFFFFFu, real);
 #pragma unroll
     for (int b = 0; b < 8; ++b) {
@@ -159,10 +174,8 @@ __global__ void __launch_bounds__(THREADS) sort_pass_kernel(PassArgs a) {
     uint32_t before = 0;
     if (real) before = whist[warp][d];
     __syncwarp();
-    if (real) {
-      rank[i] = before + __popc(peers & lt_mask);
-      if ((peers & lt_mask) == 0) whist[warp][d] = before + __popc(peers);
-    }
+    rank[i] = before + __popc(peers & lt_mask);
+    if (real && (peers & lt_mask) == 0) whist[warp][d] = before + __popc(peers);
     __syncwarp();
   }
   __syncthreads();
@@ -222,26 +235,37 @@ __global__ void __launch_bounds__(THREADS) sort_pass_kernel(PassArgs a) {
       }
       if (!failed) st_relaxed_u32(st, kFlagInclusive | (excl + count));
     }
-    out_shift[tid] = static_cast<long long>(a.digit_base[tid]) + excl - tile_start[tid];
+    out_shift[tid] = static_cast<int32_t>(a.digit_base[tid] + excl - tile_start[tid]);
   }
   if (__syncthreads_or(failed)) return;
 
-  // Scatter into shared memory in sorted order...
+  // BlockShuffle in place: keys to their sorted positions (every key of the tile is in
+  // some thread's registers), then values (read first, written after a barrier).
 #pragma unroll
   for (int i = 0; i < ITEMS; ++i) {
-    const uint32_t d = dig[i];
-    if (d < kRadix) {
-      const unsigned int lp = tile_start[d] + whist[warp][d] + rank[i];
-      skeys[lp] = key[i];
-      svals[lp] = val[i];
+    const int pos = warp * WSEG + i * kWarp + lane;
+    if (pos < valid) {
+      const uint32_t d = digit_of(key[i], a.pass);
+      rank[i] += tile_start[d] + whist[warp][d];
+      skeys[rank[i]] = key[i];
     }
   }
+#pragma unroll
+  for (int i = 0; i < ITEMS; ++i) {
+    const int pos = warp * WSEG + i * kWarp + lane;
+    key[i] = pos < valid ? svals[pos] : 0;
+  }
   __syncthreads();
-  // ...and store each digit run with consecutive addresses.
-  const int valid = static_cast<int>((a.n - tile_row) < TILE ? (a.n - tile_row) : TILE);
+#pragma unroll
+  for (int i = 0; i < ITEMS; ++i) {
+    const int pos = warp * WSEG + i * kWarp + lane;
+    if (pos < valid) svals[rank[i]] = key[i];
+  }
+  __syncthreads();
+  // BlockStore in sorted order: each digit run is written with consecutive addresses.
   for (int i = tid; i < valid; i += THREADS) {
     const int32_t k = skeys[i];
-    const long long g = out_shift[digit_of(k, a.pass)] + i;
+    const int64_t g = static_cast<int64_t>(out_shift[digit_of(k, a.pass)]) + i;
     if (g >= 0 && g < a.n) {
       a.keys_out[g] = k;
       a.vals_out[g] = svals[i];
@@ -341,7 +365,9 @@ extern "C" int crys_sort(const int32_t* keys_in, const int32_t* vals_in, int32_t
   if (n == 0) return CRYS_OK;
   if (!d_temp || !temp_bytes) return CRYS_EINVAL;
   if (*temp_bytes < L.total) return CRYS_ENOMEM;
-  if (!keys_in || !vals_in || !keys_out || !vals_out || !aligned16(keys_in)) return CRYS_EINVAL;
+  if (!keys_in || !vals_in || !keys_out || !vals_out || !aligned16(keys_in) || !aligned16(vals_in) ||
+      !aligned16(keys_out) || !aligned16(vals_out))
+    return CRYS_EINVAL;
   if (reinterpret_cast<uintptr_t>(d_temp) & 255u) return CRYS_EINVAL;
   auto overlaps = [n](const void* a, const void* b) {
     const char* x = static_cast<const char*>(a);
