@@ -114,13 +114,21 @@ int crys_project(const float* x1, const float* x2, int64_t n, float a, float b, 
 /* ------------------------------------------------------------------ hash join
  * Section 4.3: no-partitioning hash join over a linear-probing table that is a plain
  * array of 8-byte slots (no pointers).  Slot = key in the low 32 bits, value in the high
- * 32 bits; an empty slot is all ones, so key -1 cannot be stored.  Slot of key k:
- * multiplicative (Fibonacci) hashing, (uint32)(k * 2654435769) >> (32 - log2(capacity)),
- * then linear probing with wrap-around.  capacity is a power of two; the paper's tables
- * run at 50% fill, i.e. capacity = 2 * rows. */
+ * 32 bits; an empty slot is all ones, so key -1 cannot be stored.  capacity is a power of
+ * two; the paper's tables run at 50% fill, i.e. capacity = 2 * rows.  Home slot of key k:
+ *   CRYS_HASH_MULT  (0, default) multiplicative (Fibonacci) hashing,
+ *                   (uint32)(k * 2654435769) >> (32 - log2(capacity));
+ *   CRYS_HASH_IDENT (1) k mod capacity: perfect hashing when the keys are dense
+ *                   (0..n-1 with capacity >= n, as for star-schema dimension keys; the
+ *                   paper's Section 5.3 cost model assumes perfect hashing), so a table
+ *                   needs only capacity >= n and every probe reads one slot;
+ * then linear probing with wrap-around. */
+#define CRYS_HASH_MULT 0
+#define CRYS_HASH_IDENT 1
 typedef struct {
   uint64_t* slots;  /* capacity slots (device), caller-owned */
   int64_t capacity; /* power of two, >= 2 */
+  int32_t kind;     /* CRYS_HASH_MULT or CRYS_HASH_IDENT */
 } crys_hash;
 
 /* Conjunctive range predicate on a device column: lo <= col[row] <= hi. */
@@ -135,7 +143,8 @@ int crys_hash_init(const crys_hash* ht, crys_stream s);
 /* Build phase: inserts (keys[i], vals[i]) for every row i passing all `n_filters`
  * predicates (the dimension filter of a select-join query is applied at build time,
  * Section 5.3).  vals may be NULL (value 0, membership only).  Keys must be unique and
- * != -1.  Without filters the capacity must exceed n (CRYS_EFULL otherwise). */
+ * != -1.  Without filters the capacity must be at least n (CRYS_EFULL otherwise); a
+ * completely full table still answers probes (bounded by the capacity). */
 int crys_hash_build(const int32_t* keys, const int32_t* vals, int64_t n,
                     const crys_pred* filters, int32_t n_filters, const crys_hash* ht,
                     crys_stream s);

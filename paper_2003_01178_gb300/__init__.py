@@ -27,6 +27,7 @@ AGG_A, AGG_A_MUL_B, AGG_A_SUB_B, AGG_A_ADD_B = 0, 1, 2, 3
 AGG_OPS = {"sum": AGG_A, "mul": AGG_A_MUL_B, "sub": AGG_A_SUB_B, "add": AGG_A_ADD_B}
 MAX_COLS, MAX_PREDS, MAX_JOINS, MAX_PLANS, MAX_FIELD_PREDS = 16, 8, 4, 32, 2
 ACCUMULATE = 1
+HASH_MULT, HASH_IDENT = 0, 1
 OP_SELECT, OP_PROJECT, OP_PROBE, OP_PLAN, OP_SHARED_SCAN, OP_SORT = range(6)
 OP_NAMES = ["select", "project", "probe", "plan", "shared_scan", "sort"]
 
@@ -40,7 +41,7 @@ class CrystalError(RuntimeError):
 # ---------------------------------------------------------------- C structures
 
 class crys_hash(C.Structure):
-    _fields_ = [("slots", C.c_void_p), ("capacity", C.c_int64)]
+    _fields_ = [("slots", C.c_void_p), ("capacity", C.c_int64), ("kind", C.c_int32)]
 
 
 class crys_pred(C.Structure):
@@ -287,10 +288,12 @@ def project(x1: torch.Tensor, x2: torch.Tensor, a: float = 2.0, b: float = 3.0, 
     return y
 
 
-def capacity_for(rows: int) -> int:
-    """Power-of-two capacity for `rows` keys at no more than 50% fill."""
+def capacity_for(rows: int, kind: int = 0) -> int:
+    """Power-of-two capacity for `rows` keys: at most 50% fill for multiplicative
+    hashing; at least `rows` slots for identity hashing of dense keys."""
+    need = 2 * rows if kind == HASH_MULT else rows
     cap = 2
-    while cap < 2 * rows:
+    while cap < need:
         cap *= 2
     return cap
 
@@ -298,17 +301,18 @@ def capacity_for(rows: int) -> int:
 class HashTable:
     """A device linear-probing table (caller-owned slot array) and its crys_hash view."""
 
-    def __init__(self, capacity: int, device):
+    def __init__(self, capacity: int, device, kind: int = HASH_MULT):
         if capacity < 2 or capacity & (capacity - 1):
             raise ValueError("capacity must be a power of two >= 2")
         self.slots = torch.empty(capacity, dtype=torch.int64, device=device)
         self.capacity = capacity
-        self.struct = crys_hash(self.slots.data_ptr(), capacity)
+        self.kind = kind
+        self.struct = crys_hash(self.slots.data_ptr(), capacity, kind)
 
     @classmethod
     def build(cls, keys: torch.Tensor, vals: torch.Tensor | None = None, filters=(), capacity=None,
-              stream=None) -> "HashTable":
-        ht = cls(capacity or capacity_for(keys.numel()), keys.device)
+              stream=None, kind: int = HASH_MULT) -> "HashTable":
+        ht = cls(capacity or capacity_for(keys.numel(), kind), keys.device, kind)
         crys_hash_init(ht.struct, stream)
         crys_hash_build(keys, vals, keys.numel(), list(filters), ht.struct, stream)
         return ht

@@ -64,6 +64,10 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t by
                : "memory");
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar_addr, uint32_t parity) {
   uint32_t done;
   asm volatile(
@@ -160,24 +164,42 @@ __device__ __forceinline__ void st_relaxed_u32(uint32_t* p, uint32_t v) {
 
 // ---------------------------------------------------------------- hashing
 
-// Fibonacci (multiplicative) hashing: the top log2(capacity) bits of k * 2^32/phi.
-__device__ __forceinline__ uint32_t hash_slot(int32_t key, uint32_t shift) {
-  return static_cast<uint32_t>(
-      (static_cast<uint64_t>(static_cast<uint32_t>(key) * 2654435769u)) >> shift);
+// Home slot of a key: ((uint32)key * mult >> shift) & mask.  Multiplicative (Fibonacci)
+// hashing uses mult = 2654435769 (2^32/phi) and shift = 32 - log2(capacity); identity
+// hashing (key mod capacity) uses mult = 1, shift = 0.
+struct HashFn {
+  uint32_t mult, shift, mask;
+};
+
+__host__ __device__ __forceinline__ HashFn make_hash(int32_t kind, uint32_t log2cap) {
+  HashFn h;
+  h.mask = (log2cap >= 32) ? 0xFFFFFFFFu : ((1u << log2cap) - 1u);
+  if (kind == CRYS_HASH_IDENT) {
+    h.mult = 1u;
+    h.shift = 0u;
+  } else {
+    h.mult = 2654435769u;
+    h.shift = 32u - log2cap;
+  }
+  return h;
+}
+
+__device__ __forceinline__ uint32_t hash_slot(int32_t key, const HashFn& f) {
+  return ((static_cast<uint32_t>(key) * f.mult) >> f.shift) & f.mask;
 }
 
 // Looks `key` up by linear probing; returns the value, or false when absent.
-__device__ __forceinline__ bool hash_find(const uint64_t* slots, uint32_t mask, uint32_t shift,
-                                          int32_t key, int32_t* value, uint64_t pol) {
-  uint32_t h = hash_slot(key, shift);
-  for (uint32_t probe = 0; probe <= mask; ++probe) {
+__device__ __forceinline__ bool hash_find(const uint64_t* slots, const HashFn& f, int32_t key,
+                                          int32_t* value, uint64_t pol) {
+  uint32_t h = hash_slot(key, f);
+  for (uint32_t probe = 0; probe <= f.mask; ++probe) {
     uint64_t s = ld_slot(slots + h, pol);
     if (s == kEmptySlot) return false;
     if (static_cast<uint32_t>(s) == static_cast<uint32_t>(key)) {
       *value = static_cast<int32_t>(s >> 32);
       return true;
     }
-    h = (h + 1) & mask;
+    h = (h + 1) & f.mask;
   }
   return false;
 }

@@ -27,11 +27,11 @@ struct BuildArgs {
   int32_t n_filters;
   crys_pred filters[kMaxBuildFilters];
   uint64_t* slots;
-  uint32_t mask, shift;
+  HashFn hash;
   int32_t* err;
 };
 
-__global__ void __launch_bounds__(256) build_kernel(BuildArgs a) {
+__global__ void __launch_bounds__(256) build_kernel(const __grid_constant__ BuildArgs a) {
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
   for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < a.n; i += stride) {
     bool keep = true;
@@ -48,9 +48,9 @@ __global__ void __launch_bounds__(256) build_kernel(BuildArgs a) {
     }
     const uint64_t packed = static_cast<uint64_t>(static_cast<uint32_t>(key)) |
                             (static_cast<uint64_t>(static_cast<uint32_t>(val)) << 32);
-    uint32_t h = hash_slot(key, a.shift);
+    uint32_t h = hash_slot(key, a.hash);
     bool placed = false;
-    for (uint32_t probe = 0; probe <= a.mask; ++probe) {
+    for (uint32_t probe = 0; probe <= a.hash.mask; ++probe) {
       uint64_t cur = a.slots[h];
       if (cur == kEmptySlot) {
         cur = atomicCAS(reinterpret_cast<unsigned long long*>(a.slots + h), kEmptySlot, packed);
@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(256) build_kernel(BuildArgs a) {
         placed = true;
         break;
       }
-      h = (h + 1) & a.mask;
+      h = (h + 1) & a.hash.mask;
     }
     if (!placed) set_error(a.err, CRYS_DEV_TABLE_FULL);
   }
@@ -75,7 +75,7 @@ struct ProbeArgs {
   const int32_t* pay;
   int64_t n;
   const uint64_t* slots;
-  uint32_t mask, shift;
+  HashFn hash;
   unsigned long long* sum;
   unsigned long long* matches;
   int32_t* err;
@@ -150,13 +150,13 @@ __global__ void __launch_bounds__(THREADS) probe_kernel(ProbeArgs a) {
     uint64_t slot[ITEMS];
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
-      h[i] = hash_slot(key[i], a.shift);
+      h[i] = hash_slot(key[i], a.hash);
       slot[i] = (live >> i) & 1u ? ld_slot(a.slots + h[i], pol_table) : kEmptySlot;
     }
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
       int32_t value;
-      if (((live >> i) & 1u) && hash_resolve(a.slots, a.mask, h[i], slot[i], key[i], &value, pol_table)) {
+      if (((live >> i) & 1u) && hash_resolve(a.slots, a.hash.mask, h[i], slot[i], key[i], &value, pol_table)) {
         sum += static_cast<uint64_t>(static_cast<int64_t>(pay[i]) * static_cast<int64_t>(value));
         matches += 1;
       }
@@ -194,7 +194,8 @@ int launch_probe(ProbeArgs a, cudaStream_t s) {
 
 bool valid_table(const crys_hash* ht) {
   return ht && ht->slots && is_pow2(ht->capacity) && ht->capacity >= 2 &&
-         ht->capacity <= (1ll << 31) && (reinterpret_cast<uintptr_t>(ht->slots) & 7u) == 0;
+         ht->capacity <= (1ll << 31) && (reinterpret_cast<uintptr_t>(ht->slots) & 7u) == 0 &&
+         (ht->kind == CRYS_HASH_MULT || ht->kind == CRYS_HASH_IDENT);
 }
 
 int grid_for(int64_t n, int threads) {
@@ -227,7 +228,7 @@ int crys_hash_build(const int32_t* keys, const int32_t* vals, int64_t n, const c
   if (n_filters > 0 && !filters) return CRYS_EINVAL;
   if (n == 0) return CRYS_OK;
   if (!keys) return CRYS_EINVAL;
-  if (n_filters == 0 && ht->capacity <= n) return CRYS_EFULL;
+  if (n_filters == 0 && ht->capacity < n) return CRYS_EFULL;
   BuildArgs a;
   a.keys = keys;
   a.vals = vals;
@@ -238,8 +239,7 @@ int crys_hash_build(const int32_t* keys, const int32_t* vals, int64_t n, const c
     a.filters[f] = filters[f];
   }
   a.slots = ht->slots;
-  a.mask = static_cast<uint32_t>(ht->capacity - 1);
-  a.shift = 32u - log2_pow2(static_cast<uint64_t>(ht->capacity));
+  a.hash = make_hash(ht->kind, log2_pow2(static_cast<uint64_t>(ht->capacity)));
   a.err = device_error_word();
   if (!a.err) return CRYS_ECUDA;
   build_kernel<<<grid_for(n, 256), 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(a);
@@ -261,8 +261,7 @@ int crys_probe_aggregate(const int32_t* fk, const int32_t* payload, int64_t n, c
   a.pay = payload;
   a.n = n;
   a.slots = ht->slots;
-  a.mask = static_cast<uint32_t>(ht->capacity - 1);
-  a.shift = 32u - log2_pow2(static_cast<uint64_t>(ht->capacity));
+  a.hash = make_hash(ht->kind, log2_pow2(static_cast<uint64_t>(ht->capacity)));
   a.sum = reinterpret_cast<unsigned long long*>(d_sum);
   a.matches = reinterpret_cast<unsigned long long*>(d_matches);
   a.err = device_error_word();

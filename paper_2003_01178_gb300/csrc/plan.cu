@@ -27,7 +27,7 @@ constexpr int kMaxProbes = 8;  // distinct (fk column, table) pairs probed once 
 
 struct DevJoin {
   const uint64_t* slots;
-  uint32_t mask, shift;  // table capacity - 1, hash shift
+  HashFn hash;
   int32_t fk_col;
   int32_t card;    // 0: not grouped
   int32_t stride;  // mixed-radix weight of this join's group code
@@ -35,7 +35,9 @@ struct DevJoin {
   int32_t n_fp;
   uint32_t fp_shift[CRYS_MAX_FIELD_PREDS], fp_mask[CRYS_MAX_FIELD_PREDS];
   int32_t fp_lo[CRYS_MAX_FIELD_PREDS], fp_hi[CRYS_MAX_FIELD_PREDS];
-  int32_t probe;  // index of the batch-wide probe that serves this join, -1: probe here
+  uint32_t fp_span[CRYS_MAX_FIELD_PREDS];  // hi - lo (an empty range has mask 0, lo 1, span 0)
+  int32_t probe;    // index of the batch-wide probe that serves this join, -1: probe here
+  int32_t fk_slot;  // staged slice of fk_col (shared scan)
 };
 
 struct DevQuery {
@@ -43,9 +45,15 @@ struct DevQuery {
   int32_t pred_col[CRYS_MAX_PREDS];
   int32_t pred_lo[CRYS_MAX_PREDS];
   int32_t pred_hi[CRYS_MAX_PREDS];
+  uint32_t pred_span[CRYS_MAX_PREDS];  // hi - lo
+  int32_t pred_slot[CRYS_MAX_PREDS];   // staged slice of pred_col (shared scan)
+  int32_t never;                       // an empty range: no row can qualify
   int32_t n_joins;
   DevJoin joins[CRYS_MAX_JOINS];
   int32_t agg_op, agg_a, agg_b;
+  int32_t agg_a_slot, agg_b_slot;      // staged slices (shared scan)
+  int32_t first_join;                  // shared scan: join tested on every row (-1: none)
+  int32_t first_pred;                  // shared scan: fact predicate tested on every row (-1)
   int32_t acc_mode;
   int32_t acc_off;  // first shared-memory accumulator of this query
   int64_t groups;
@@ -75,6 +83,33 @@ struct GlobalCols {
   }
 };
 
+// Column loads that stay in L1: the columns a shared scan's queries read for predicates
+// and aggregates are read by several queries of the batch in a row.
+__device__ __forceinline__ int4 ld_cached_v4(const int32_t* p) {
+  int4 v;
+  asm volatile("ld.global.nc.v4.s32 {%0,%1,%2,%3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ int32_t ld_cached(const int32_t* p) {
+  int32_t v;
+  asm volatile("ld.global.nc.s32 %0, [%1];" : "=r"(v) : "l"(p));
+  return v;
+}
+
+struct CachedCols {
+  const int32_t* const* cols;
+  int64_t row0;
+  int valid;
+  __device__ __forceinline__ int4 load4(int c, int p) const {
+    const int32_t* src = cols[c] + row0 + p;
+    if (p + 4 <= valid) return ld_cached_v4(src);
+    int v[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) v[e] = p + e < valid ? ld_cached(src + e) : 0;
+    return make_int4(v[0], v[1], v[2], v[3]);
+  }
+};
+
 // Column access from the shared-memory stage (shared_scan_kernel).
 struct StagedCols {
   const int32_t* const* cols;
@@ -85,6 +120,16 @@ struct StagedCols {
   int valid, bulk;
   __device__ __forceinline__ int4 load4(int c, int p) const {
     return stage_read4(stage + slot_of[c] * tile, cols[c] + row0, p, bulk, valid);
+  }
+  // One value of column c (staged in slice `slot`) at tile row r < valid.
+  __device__ __forceinline__ int32_t value(int slot, int c, int r) const {
+    return r < bulk ? stage[slot * tile + r] : cols[c][row0 + r];
+  }
+  // Column c known to be staged in slice `slot`.
+  __device__ __forceinline__ int4 load4s(int slot, int c, int p) const {
+    const int32_t* st = stage + slot * tile;
+    if (p + 4 <= bulk) return *reinterpret_cast<const int4*>(st + p);
+    return stage_read4(st, cols[c] + row0, p, bulk, valid);
   }
 };
 
@@ -105,14 +150,15 @@ __device__ __forceinline__ void unpack4(int4 q, int32_t* dst) {
 // Probes one table for this thread's ITEMS rows: all first-slot reads are issued before
 // any is resolved.  Returns the bitmap of rows whose key was found; values in `value`.
 template <int ITEMS>
-__device__ __forceinline__ uint32_t probe_items(const uint64_t* slots, uint32_t mask, uint32_t shift,
+__device__ __forceinline__ uint32_t probe_items(const uint64_t* slots, const HashFn& hf,
                                                 const int32_t (&key)[ITEMS], uint32_t live,
                                                 int32_t (&value)[ITEMS], uint64_t pol) {
+  const uint32_t mask = hf.mask;
   uint32_t h[ITEMS];
   uint64_t slot[ITEMS];
 #pragma unroll
   for (int i = 0; i < ITEMS; ++i) {
-    h[i] = hash_slot(key[i], shift);
+    h[i] = hash_slot(key[i], hf);
     slot[i] = ((live >> i) & 1u) ? ld_slot(slots + h[i], pol) : kEmptySlot;
   }
   uint32_t found = 0;
@@ -169,7 +215,7 @@ __device__ __forceinline__ uint32_t eval_query(const DevQuery& q, const Cols& co
         else
           key[4 * j] = key[4 * j + 1] = key[4 * j + 2] = key[4 * j + 3] = 0;
       }
-      alive &= probe_items<ITEMS>(J.slots, J.mask, J.shift, key, alive, value, pol_table);
+      alive &= probe_items<ITEMS>(J.slots, J.hash, key, alive, value, pol_table);
     }
     for (int f = 0; f < J.n_fp; ++f) {
       const uint32_t sh = J.fp_shift[f], mk = J.fp_mask[f];
@@ -195,6 +241,140 @@ __device__ __forceinline__ uint32_t eval_query(const DevQuery& q, const Cols& co
   }
   if (!alive) return 0;
   // BlockLoadSel of the aggregate operands and the expression in int64.
+#pragma unroll
+  for (int j = 0; j < VEC; ++j) {
+    if (!((alive >> (4 * j)) & 0xFu)) continue;
+    const int p = (j * THREADS + tid) * 4;
+    int32_t va[4], vb[4] = {0, 0, 0, 0};
+    unpack4(cols.load4(q.agg_a, p), va);
+    if (q.agg_op != CRYS_AGG_A) unpack4(cols.load4(q.agg_b, p), vb);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int64_t x = va[e], y = vb[e];
+      int64_t r;
+      switch (q.agg_op) {
+        case CRYS_AGG_A_MUL_B: r = x * y; break;
+        case CRYS_AGG_A_SUB_B: r = x - y; break;
+        case CRYS_AGG_A_ADD_B: r = x + y; break;
+        default: r = x; break;
+      }
+      val[4 * j + e] = r;
+    }
+  }
+  return alive;
+}
+
+// Range test lo <= v <= hi as one unsigned comparison (span = hi - lo).
+__device__ __forceinline__ bool in_span(int32_t v, int32_t lo, uint32_t span) {
+  return static_cast<uint32_t>(v) - static_cast<uint32_t>(lo) <= span;
+}
+
+// Evaluation of one query of a shared scan on this thread's rows, cheapest tests first:
+// (1) dimension predicates on values probed once for the batch (found bits, then bit
+// fields of the 16-byte vectors of probed values; the join chosen on the host as most
+// selective first), (2) fact predicates, (3) joins this query alone uses (probed now, for
+// surviving rows only), (4) group codes and the aggregate, only while a row survives.
+// Probed values for probe d, vector j of thread t at pv[(d * VEC + j) * THREADS + t];
+// found bits at pf[d * THREADS + t].
+template <int THREADS, int ITEMS>
+__device__ __forceinline__ uint32_t eval_shared(const DevQuery& q, const CachedCols& cols, uint32_t alive,
+                                                const int4* pv, const uint32_t* pf,
+                                                int32_t (&gid)[ITEMS], int64_t (&val)[ITEMS],
+                                                int32_t* err, uint64_t pol_table) {
+  constexpr int VEC = ITEMS / 4;
+  const int tid = threadIdx.x;
+  if (q.never) return 0;
+  // (1)
+  for (int k = -1; k < q.n_joins && alive; ++k) {
+    const int jn = k < 0 ? q.first_join : k;
+    if (jn < 0 || (k >= 0 && jn == q.first_join)) continue;
+    const DevJoin& J = q.joins[jn];
+    if (J.probe < 0) continue;
+    alive &= pf[J.probe * THREADS + tid];
+    for (int f = 0; f < J.n_fp && alive; ++f) {
+      const uint32_t sh = J.fp_shift[f], mk = J.fp_mask[f], span = J.fp_span[f];
+      const int32_t lo = J.fp_lo[f];
+#pragma unroll
+      for (int j = 0; j < VEC; ++j) {
+        const int4 v4 = pv[(J.probe * VEC + j) * THREADS + tid];
+        const int32_t v[4] = {v4.x, v4.y, v4.z, v4.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+          if (!in_span(field_of(v[e], sh, mk), lo, span)) alive &= ~(1u << (4 * j + e));
+      }
+    }
+  }
+  // (2)
+  for (int f = 0; f < q.n_preds && alive; ++f) {
+    const int c = q.pred_col[f];
+    const int32_t lo = q.pred_lo[f];
+    const uint32_t span = q.pred_span[f];
+#pragma unroll
+    for (int j = 0; j < VEC; ++j) {
+      if (!((alive >> (4 * j)) & 0xFu)) continue;
+      int32_t v[4];
+      unpack4(cols.load4(c, (j * THREADS + tid) * 4), v);
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+        if (!in_span(v[e], lo, span)) alive &= ~(1u << (4 * j + e));
+    }
+  }
+  if (!alive) return 0;
+#pragma unroll
+  for (int i = 0; i < ITEMS; ++i) gid[i] = 0;
+  // (3) joins served by no batch-wide probe
+  for (int jn = 0; jn < q.n_joins && alive; ++jn) {
+    const DevJoin& J = q.joins[jn];
+    if (J.probe >= 0) continue;
+    int32_t key[ITEMS], value[ITEMS];
+#pragma unroll
+    for (int j = 0; j < VEC; ++j) {
+      if ((alive >> (4 * j)) & 0xFu)
+        unpack4(cols.load4(J.fk_col, (j * THREADS + tid) * 4), key + 4 * j);
+      else
+        key[4 * j] = key[4 * j + 1] = key[4 * j + 2] = key[4 * j + 3] = 0;
+    }
+    alive &= probe_items<ITEMS>(J.slots, J.hash, key, alive, value, pol_table);
+    for (int f = 0; f < J.n_fp; ++f) {
+#pragma unroll
+      for (int i = 0; i < ITEMS; ++i)
+        if (!in_span(field_of(value[i], J.fp_shift[f], J.fp_mask[f]), J.fp_lo[f], J.fp_span[f]))
+          alive &= ~(1u << i);
+    }
+    if (J.card > 0) {
+#pragma unroll
+      for (int i = 0; i < ITEMS; ++i) {
+        const uint32_t code = static_cast<uint32_t>(field_of(value[i], J.gshift, J.gmask));
+        if (((alive >> i) & 1u) && code >= static_cast<uint32_t>(J.card)) {
+          set_error(err, CRYS_DEV_BAD_GROUP);
+          alive &= ~(1u << i);
+        }
+        gid[i] += static_cast<int32_t>(code) * J.stride;
+      }
+    }
+  }
+  if (!alive) return 0;
+  // (4)
+  for (int jn = 0; jn < q.n_joins; ++jn) {
+    const DevJoin& J = q.joins[jn];
+    if (J.probe < 0 || J.card <= 0) continue;
+    const uint32_t card = static_cast<uint32_t>(J.card);
+#pragma unroll
+    for (int j = 0; j < VEC; ++j) {
+      const int4 v4 = pv[(J.probe * VEC + j) * THREADS + tid];
+      const int32_t v[4] = {v4.x, v4.y, v4.z, v4.w};
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int i = 4 * j + e;
+        const uint32_t code = static_cast<uint32_t>(field_of(v[e], J.gshift, J.gmask));
+        if (((alive >> i) & 1u) && code >= card) {
+          set_error(err, CRYS_DEV_BAD_GROUP);
+          alive &= ~(1u << i);
+        }
+        gid[i] += static_cast<int32_t>(code) * J.stride;
+      }
+    }
+  }
 #pragma unroll
   for (int j = 0; j < VEC; ++j) {
     if (!((alive >> (4 * j)) & 0xFu)) continue;
@@ -329,8 +509,9 @@ __global__ void __launch_bounds__(THREADS) plan_kernel(const __grid_constant__ P
 
 struct ProbeSpec {
   const uint64_t* slots;
-  uint32_t mask, shift;
+  HashFn hash;
   int32_t fk_col;
+  int32_t fk_slot;  // staged slice of fk_col
 };
 
 struct ScanArgs {
@@ -348,104 +529,93 @@ struct ScanArgs {
   DevQuery q[CRYS_MAX_PLANS];
 };
 
+// The shared scan keeps no staging ring: each thread loads its own rows' foreign keys
+// (16-byte vectors, read once per tile for the whole batch) and probes every shared
+// dimension table once; predicate and aggregate columns are read with L1-cached loads,
+// so the second and later queries of the batch that read a column find the tile in L1.
+// Shared memory holds only each thread's probe results and the group accumulators,
+// which keeps several blocks per SM resident to hide the probes' latency; no barrier is
+// needed inside the tile loop.
 template <int THREADS, int ITEMS>
-__global__ void __launch_bounds__(THREADS) shared_scan_kernel(const __grid_constant__ ScanArgs a) {
+__global__ void __launch_bounds__(THREADS, (24 * kWarp) / THREADS > 0 ? (24 * kWarp) / THREADS : 1)
+    shared_scan_kernel(const __grid_constant__ ScanArgs a) {
   constexpr int TILE = THREADS * ITEMS;
   constexpr int VEC = ITEMS / 4;
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  __shared__ StageRing ring;
-  const int S = a.stages;
   const int tid = threadIdx.x, lane = tid % kWarp;
-  // dynamic shared memory: stages | probed values | probed found bits | accumulators
-  int32_t* stages = reinterpret_cast<int32_t*>(smem_raw);
-  const size_t stage_elems = static_cast<size_t>(a.n_union) * TILE;
-  int32_t* pvalues = stages + S * stage_elems;
-  uint32_t* pfound = reinterpret_cast<uint32_t*>(pvalues + static_cast<size_t>(a.n_probes) * TILE);
-  const SharedAcc acc = shared_acc(reinterpret_cast<unsigned char*>(pfound + a.n_probes * THREADS),
+  int4* pv = reinterpret_cast<int4*>(smem_raw);                                   // probes x TILE
+  uint32_t* pf = reinterpret_cast<uint32_t*>(pv + static_cast<size_t>(a.n_probes) * VEC * THREADS);
+  const SharedAcc acc = shared_acc(reinterpret_cast<unsigned char*>(pf + a.n_probes * THREADS),
                                    a.shared_groups);
   for (int g = tid; g < a.shared_groups; g += THREADS) {
     acc.sums[g] = 0;
     acc.counts[g] = 0;
   }
+  __syncthreads();
 
   const int64_t nrows = a.row_end - a.row_begin;
   const int64_t ntiles = (nrows + TILE - 1) / TILE;
   const uint64_t pol = policy_evict_first();
   const uint64_t pol_table = policy_evict_last();
-  int64_t issued = 0;
-  const int32_t* ucols[CRYS_MAX_COLS];
-  for (int u = 0; u < a.n_union; ++u) ucols[u] = a.cols[a.union_cols[u]];
-
-  auto issue = [&](int s) {
-    const int64_t t = static_cast<int64_t>(blockIdx.x) + issued * gridDim.x;
-    ++issued;
-    if (t >= ntiles) {
-      ring.tile[s] = -1;
-      return;
-    }
-    ring.tile[s] = t;
-    const int64_t row = a.row_begin + t * TILE;
-    const int64_t valid = (nrows - t * TILE) < TILE ? (nrows - t * TILE) : TILE;
-    ring_issue(&ring.full[s], stages + s * stage_elems, TILE, ucols, a.n_union, row, valid, pol);
-  };
-
-  if (tid == 0) {
-    for (int s = 0; s < S; ++s) {
-      mbar_init(&ring.full[s], 1);
-      ring.tile[s] = -1;
-    }
-    fence_barrier_init();
-  }
-  __syncthreads();
-  if (tid == 0)
-    for (int s = 0; s < S; ++s) issue(s);
-  __syncthreads();
-
-  const Probed probed = {pvalues, pfound};
-  bool aborted = false;
-  for (int64_t k = 0;; ++k) {
-    const int s = static_cast<int>(k % S);
-    const int64_t t = ring.tile[s];
-    if (t < 0) break;
-    const bool ok = mbar_wait_bounded(&ring.full[s], static_cast<uint32_t>((k / S) & 1), a.err);
-    if (__syncthreads_or(!ok)) {
-      if (tid == 0) {
-        for (int j = 0; j < S; ++j) {
-          const int64_t kk = k + j;
-          const int ss = static_cast<int>(kk % S);
-          if (ring.tile[ss] >= 0)
-            mbar_wait_bounded(&ring.full[ss], static_cast<uint32_t>((kk / S) & 1), a.err);
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int64_t row0 = a.row_begin + t * TILE;
+    const int valid = static_cast<int>((nrows - t * TILE) < TILE ? (nrows - t * TILE) : TILE);
+    const uint32_t live = rows_present<THREADS, ITEMS>(valid);
+    GlobalCols fk_cols;
+    fk_cols.cols = a.cols;
+    fk_cols.row0 = row0;
+    fk_cols.valid = valid;
+    fk_cols.pol = pol;
+    // Batch-wide BlockLookup: each shared (fk column, table) pair once per row; up to PW
+    // probes at a time with all their first-slot reads in flight together.
+    constexpr int PW = ITEMS <= 4 ? 2 : 1;
+    for (int d0 = 0; d0 < a.n_probes; d0 += PW) {
+      int32_t key[PW][ITEMS];
+      uint32_t h[PW][ITEMS];
+      uint64_t slot[PW][ITEMS];
+#pragma unroll
+      for (int dd = 0; dd < PW; ++dd) {
+        if (d0 + dd >= a.n_probes) break;
+        const ProbeSpec& P = a.probes[d0 + dd];
+#pragma unroll
+        for (int j = 0; j < VEC; ++j) unpack4(fk_cols.load4(P.fk_col, (j * THREADS + tid) * 4), key[dd] + 4 * j);
+#pragma unroll
+        for (int i = 0; i < ITEMS; ++i) {
+          h[dd][i] = hash_slot(key[dd][i], P.hash);
+          slot[dd][i] = ((live >> i) & 1u) ? ld_slot(P.slots + h[dd][i], pol_table) : kEmptySlot;
         }
       }
-      aborted = true;
-      break;
+#pragma unroll
+      for (int dd = 0; dd < PW; ++dd) {
+        const int d = d0 + dd;
+        if (d >= a.n_probes) break;
+        const ProbeSpec& P = a.probes[d];
+        int32_t value[ITEMS];
+        uint32_t found = 0;
+#pragma unroll
+        for (int i = 0; i < ITEMS; ++i) {
+          value[i] = 0;
+          if (((live >> i) & 1u) &&
+              hash_resolve(P.slots, P.hash.mask, h[dd][i], slot[dd][i], key[dd][i], &value[i], pol_table))
+            found |= 1u << i;
+        }
+        pf[d * THREADS + tid] = found;
+#pragma unroll
+        for (int j = 0; j < VEC; ++j)
+          pv[(d * VEC + j) * THREADS + tid] = make_int4(value[4 * j], value[4 * j + 1], value[4 * j + 2], value[4 * j + 3]);
+      }
     }
-    StagedCols cols;
+    CachedCols cols;
     cols.cols = a.cols;
-    cols.slot_of = a.slot_of;
-    cols.stage = stages + s * stage_elems;
-    cols.tile = TILE;
-    cols.row0 = a.row_begin + t * TILE;
-    cols.valid = static_cast<int>((nrows - t * TILE) < TILE ? (nrows - t * TILE) : TILE);
-    cols.bulk = cols.valid & ~3;
-    const uint32_t live = rows_present<THREADS, ITEMS>(cols.valid);
-    // Batch-wide BlockLookup: each distinct (fk column, table) pair once per row.  Each
-    // thread keeps the results of its own rows, so no barrier is needed before use.
-    for (int d = 0; d < a.n_probes; ++d) {
-      const ProbeSpec& P = a.probes[d];
-      int32_t key[ITEMS], value[ITEMS];
-#pragma unroll
-      for (int j = 0; j < VEC; ++j) unpack4(cols.load4(P.fk_col, (j * THREADS + tid) * 4), key + 4 * j);
-      pfound[d * THREADS + tid] = probe_items<ITEMS>(P.slots, P.mask, P.shift, key, live, value, pol_table);
-#pragma unroll
-      for (int i = 0; i < ITEMS; ++i) pvalues[(d * ITEMS + i) * THREADS + tid] = value[i];
-    }
+    cols.row0 = row0;
+    cols.valid = valid;
     for (int qi = 0; qi < a.n_queries; ++qi) {
       const DevQuery& q = a.q[qi];
       int32_t gid[ITEMS];
       int64_t val[ITEMS];
-      const uint32_t alive = eval_query<THREADS, ITEMS>(q, cols, live, probed, gid, val, a.err, pol_table);
+      const uint32_t alive = eval_shared<THREADS, ITEMS>(q, cols, live, pv, pf, gid, val, a.err, pol_table);
       if (q.acc_mode == kAccSingle) {
+        if (!__any_sync(0xFFFFFFFFu, alive != 0)) continue;
         uint64_t s_sum = 0, s_cnt = 0;
 #pragma unroll
         for (int i = 0; i < ITEMS; ++i) {
@@ -474,13 +644,7 @@ __global__ void __launch_bounds__(THREADS) shared_scan_kernel(const __grid_const
         }
       }
     }
-    __syncthreads();
-    if (tid == 0) {
-      fence_proxy_async_smem();
-      issue(s);
-    }
   }
-  if (aborted) return;
   __syncthreads();
   for (int qi = 0; qi < a.n_queries; ++qi) {
     const DevQuery& q = a.q[qi];
@@ -512,6 +676,7 @@ __global__ void __launch_bounds__(256) pack_kernel(const __grid_constant__ PackA
 
 constexpr int64_t kMaxGroups = 1ll << 28;
 constexpr size_t kSharedBudget = 200 * 1024;  // dynamic shared memory a block may use
+constexpr int kScanBlocksPerSM = 3;           // shared-scan blocks resident per SM (target)
 
 uint32_t field_mask(int32_t bits) {
   return (bits <= 0 || bits >= 32) ? 0xFFFFFFFFu : ((1u << bits) - 1u);
@@ -552,8 +717,12 @@ int to_device(const crys_table& t, const crys_plan& p, DevQuery* d, uint32_t* co
     d->pred_col[f] = p.preds[f].col;
     d->pred_lo[f] = p.preds[f].lo;
     d->pred_hi[f] = p.preds[f].hi;
+    d->pred_span[f] = static_cast<uint32_t>(p.preds[f].hi) - static_cast<uint32_t>(p.preds[f].lo);
     mask |= 1u << p.preds[f].col;
   }
+  d->never = 0;
+  for (int f = 0; f < p.n_preds; ++f)
+    if (p.preds[f].lo > p.preds[f].hi) d->never = 1;
   d->n_joins = p.n_joins;
   // mixed-radix weights: first grouped join most significant
   int64_t weight = groups;
@@ -561,13 +730,12 @@ int to_device(const crys_table& t, const crys_plan& p, DevQuery* d, uint32_t* co
     const crys_join& J = p.joins[j];
     DevJoin& D = d->joins[j];
     if (!col_ok(J.fk_col) || !J.ht.slots || !is_pow2(J.ht.capacity) || J.ht.capacity < 2 ||
-        J.ht.capacity > (1ll << 31))
+        J.ht.capacity > (1ll << 31) || (J.ht.kind != CRYS_HASH_MULT && J.ht.kind != CRYS_HASH_IDENT))
       return CRYS_EINVAL;
     if (!field_ok(J.group_shift, J.group_bits) || J.n_preds < 0 || J.n_preds > CRYS_MAX_FIELD_PREDS)
       return CRYS_EINVAL;
     D.slots = J.ht.slots;
-    D.mask = static_cast<uint32_t>(J.ht.capacity - 1);
-    D.shift = 32u - log2_pow2(static_cast<uint64_t>(J.ht.capacity));
+    D.hash = make_hash(J.ht.kind, log2_pow2(static_cast<uint64_t>(J.ht.capacity)));
     D.fk_col = J.fk_col;
     D.card = J.group_card;
     D.stride = 0;
@@ -584,6 +752,12 @@ int to_device(const crys_table& t, const crys_plan& p, DevQuery* d, uint32_t* co
       D.fp_mask[f] = field_mask(J.preds[f].bits);
       D.fp_lo[f] = J.preds[f].lo;
       D.fp_hi[f] = J.preds[f].hi;
+      D.fp_span[f] = static_cast<uint32_t>(J.preds[f].hi) - static_cast<uint32_t>(J.preds[f].lo);
+      if (J.preds[f].lo > J.preds[f].hi) {  // never true: compare the constant 0 with [1, 1]
+        D.fp_mask[f] = 0;
+        D.fp_lo[f] = 1;
+        D.fp_span[f] = 0;
+      }
     }
     D.probe = -1;
     mask |= 1u << J.fk_col;
@@ -648,14 +822,13 @@ int launch_plan(PlanArgs& a, cudaStream_t s) {
 template <int THREADS, int ITEMS>
 int launch_scan(ScanArgs& a, cudaStream_t s) {
   constexpr int TILE = THREADS * ITEMS;
-  const size_t stage_bytes = static_cast<size_t>(a.n_union) * TILE * sizeof(int32_t);
   const size_t probe_bytes = static_cast<size_t>(a.n_probes) * (TILE + THREADS) * sizeof(int32_t);
-  // Shared-memory accumulators for as many queries as fit next to two stages and the
-  // probe results; the rest accumulate with global atomics.
-  const size_t fixed = 2 * stage_bytes + probe_bytes;
-  const size_t budget = kSharedBudget > fixed ? kSharedBudget - fixed : 0;
-  // Smallest group counts first: they have the most rows per group, where global
-  // atomics would contend most.
+  // Shared memory per block: probe results plus accumulators for as many queries as
+  // fit (smallest group counts first: they have the most rows per group, where global
+  // atomics would contend most) within a share that keeps kScanBlocksPerSM blocks
+  // resident; the rest accumulate with global atomics.
+  const size_t share = (220u * 1024u) / kScanBlocksPerSM;
+  const size_t budget = share > probe_bytes ? share - probe_bytes : 0;
   int order[CRYS_MAX_PLANS];
   for (int qi = 0; qi < a.n_queries; ++qi) order[qi] = qi;
   for (int i = 1; i < a.n_queries; ++i)
@@ -676,14 +849,7 @@ int launch_scan(ScanArgs& a, cudaStream_t s) {
     }
   }
   a.shared_groups = static_cast<int32_t>(used);
-  const size_t acc_bytes = static_cast<size_t>(used) * 12;
-  {
-    const size_t room = kSharedBudget - probe_bytes - acc_bytes;  // >= 2 stages by construction
-    size_t st = room / (stage_bytes > 0 ? stage_bytes : 1);
-    a.stages = static_cast<int32_t>(st < 2 ? 2 : (st > kMaxStages ? kMaxStages : st));
-  }
-  const size_t smem = a.stages * stage_bytes + probe_bytes + acc_bytes;
-  if (smem > 227 * 1024) return CRYS_EINVAL;
+  const size_t smem = probe_bytes + static_cast<size_t>(used) * 12;
   auto k = shared_scan_kernel<THREADS, ITEMS>;
   if (!allow_smem(k, smem)) return CRYS_ECUDA;
   const int64_t ntiles = (a.row_end - a.row_begin + TILE - 1) / TILE;
@@ -706,7 +872,8 @@ void assign_probes(ScanArgs& a) {
   Pair pairs[CRYS_MAX_PLANS * CRYS_MAX_JOINS];
   int n = 0;
   auto same = [](const ProbeSpec& p, const DevJoin& J) {
-    return p.slots == J.slots && p.fk_col == J.fk_col && p.mask == J.mask;
+    return p.slots == J.slots && p.fk_col == J.fk_col && p.hash.mask == J.hash.mask &&
+           p.hash.mult == J.hash.mult;
   };
   for (int qi = 0; qi < a.n_queries; ++qi) {
     for (int j = 0; j < a.q[qi].n_joins; ++j) {
@@ -715,7 +882,7 @@ void assign_probes(ScanArgs& a) {
       for (int d = 0; d < n && found < 0; ++d)
         if (same(pairs[d].spec, J)) found = d;
       if (found < 0) {
-        pairs[n].spec = {J.slots, J.mask, J.shift, J.fk_col};
+        pairs[n].spec = {J.slots, J.hash, J.fk_col, 0};
         pairs[n].uses = 0;
         found = n++;
       }
@@ -833,6 +1000,40 @@ int crys_run_plans(const crys_table* fact, const crys_plan* plans, int32_t n_pla
     }
   }
   assign_probes(*a);
+  // staged slices of every column a query or probe reads
+  for (int qi = 0; qi < n_plans; ++qi) {
+    DevQuery& q = a->q[qi];
+    for (int f = 0; f < q.n_preds; ++f) q.pred_slot[f] = a->slot_of[q.pred_col[f]];
+    q.agg_a_slot = a->slot_of[q.agg_a];
+    q.agg_b_slot = a->slot_of[q.agg_b];
+    for (int j = 0; j < q.n_joins; ++j) q.joins[j].fk_slot = a->slot_of[q.joins[j].fk_col];
+  }
+  for (int d = 0; d < a->n_probes; ++d) a->probes[d].fk_slot = a->slot_of[a->probes[d].fk_col];
+  // The filter each query tests on every row of a tile: the batch-probed join whose
+  // predicates keep the smallest share of their fields' value range (codes assumed
+  // spread over the field), else the first fact predicate, else none.
+  for (int qi = 0; qi < n_plans; ++qi) {
+    DevQuery& q = a->q[qi];
+    q.first_join = -1;
+    q.first_pred = -1;
+    double best = 2.0;
+    for (int j = 0; j < q.n_joins; ++j) {
+      const DevJoin& J = q.joins[j];
+      if (J.probe < 0 || J.n_fp == 0) continue;
+      double est = 1.0;
+      for (int f = 0; f < J.n_fp; ++f) {
+        const double top = static_cast<double>(J.fp_mask[f]);
+        const double lo = J.fp_lo[f] < 0 ? 0.0 : static_cast<double>(J.fp_lo[f]);
+        const double hi = static_cast<double>(J.fp_hi[f]) > top ? top : static_cast<double>(J.fp_hi[f]);
+        est *= hi >= lo ? (hi - lo + 1.0) / (top + 1.0) : 0.0;
+      }
+      if (est < best) {
+        best = est;
+        q.first_join = j;
+      }
+    }
+    if (q.first_join < 0 && q.n_preds > 0) q.first_pred = 0;
+  }
   a->row_begin = row_begin;
   a->row_end = row_end;
   a->err = device_error_word();

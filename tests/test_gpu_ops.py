@@ -119,6 +119,21 @@ def test_probe_parity(crys, orc, nb, np_, variant):
     crys.crys_set_tile(crys.OP_PROBE, 0)
 
 
+@pytest.mark.parametrize("dense", [True, False])
+def test_probe_identity_hash(crys, orc, dense):
+    # identity hashing: collision-free for dense keys (capacity >= n), linear probing
+    # resolves the collisions of sparse keys
+    nb = 100_000
+    bk = datagen.perm_i32(5, 1, nb) if dense else datagen.perm_i32(5, 1, nb) * 3 + 5  # never -1
+    bv = datagen.uniform_i32(5, 2, nb, -100, 100)
+    fk = datagen.uniform_i32(5, 3, 1_000_003, -10, 3 * nb)
+    pay = datagen.uniform_i32(5, 4, 1_000_003, 1, 100)
+    cap = crys.capacity_for(nb, crys.HASH_IDENT) * (1 if dense else 2)
+    ht = crys.HashTable.build(_dev(bk), _dev(bv), capacity=cap, kind=crys.HASH_IDENT)
+    s, m = crys.probe_aggregate(_dev(fk), _dev(pay), ht)
+    assert (int(s.item()), int(m.item())) == orc.join_sum(bk, bv, fk, pay)
+
+
 def test_hash_table_contents(crys):
     n = 50_000
     keys = datagen.perm_i32(3, 4, n) * 7 - 100_000       # sparse, negative keys
