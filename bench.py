@@ -485,20 +485,30 @@ def run_operator(args, rank, world, local):
             line = op_line(args, world, "sort", n / (avg / 1e3) / 1e6, "Mkeys/s", "sort_pass_kernel", 68 * n, avg,
                            {"rows": n, "l2": "inputs larger than L2", "passes": "4 x 8-bit, stable"})
         elif args.workload == "q1":
-            n = args.rows or (1 << 22)
-            t = dgd.q1_tables(seed, n, dev)
-            f, d = t["fact"], t["dim"]
-            ht = crys.HashTable.build(d["key"], d["yr"], filters=[(d["yr"], 3, 3)])
-            sums = torch.zeros(1, dtype=torch.int64, device=dev)
-            cnts = torch.zeros(1, dtype=torch.int64, device=dev)
-            table = crys.make_table([f["fk"], f["a"], f["b"], f["c"]])
-            plan = crys.make_plan([(1, -(1 << 31), 24), (2, 1, 3)], [(0, ht, 0)], ("mul", 3, 2), sums, cnts)
+            sizes = [args.rows] if args.rows else [1 << 22, 1 << 28]
+            results = {}
             flush_buf = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
-            ms = time_launches(lambda: crys.crys_run_plan(table, plan), args.steps, args.warmup, stream,
-                               flush=lambda: l2_flush(flush_buf))
-            avg = statistics.median(ms)
+            for n in sizes:
+                t = dgd.q1_tables(seed, n, dev)
+                f, d = t["fact"], t["dim"]
+                ht = crys.HashTable.build(d["key"], d["yr"], filters=[(d["yr"], 3, 3)])
+                sums = torch.zeros(1, dtype=torch.int64, device=dev)
+                cnts = torch.zeros(1, dtype=torch.int64, device=dev)
+                table = crys.make_table([f["fk"], f["a"], f["b"], f["c"]])
+                plan = crys.make_plan([(1, -(1 << 31), 24), (2, 1, 3)], [(0, ht, 0)], ("mul", 3, 2), sums, cnts)
+                ms = time_launches(lambda: crys.crys_run_plan(table, plan), args.steps, args.warmup, stream,
+                                   flush=lambda: l2_flush(flush_buf))
+                results[n] = statistics.median(ms)
+                del t, f, d, ht, table, plan
+            n = sizes[0]
+            avg = results[n]
+            extra = {"by_rows": {str(k): {"ms": round(v, 4), "GB/s": round(16 * k / (v / 1e3) / 1e9, 1),
+                                          "frac": round(16 * k / (v / 1e3) / 1e9 / measured_hbm_peak()[0], 4)}
+                                 for k, v in results.items()}}
             line = op_line(args, world, "q1", 16 * n / (avg / 1e3) / 1e9, "GB/s", "plan_kernel", 16 * n, avg,
-                           {"rows": n, "dtype": "int64", "l2": "flushed between timed launches (512 MB write)"})
+                           {"rows": n, "dtype": "int64", "l2": "flushed between timed launches (512 MB write)",
+                            "query": "yr == 3 AND a < 25 AND 1 <= b <= 3, SUM(c * b), 2556-row date-like dimension"},
+                           extra)
         else:
             raise SystemExit(f"unknown workload {args.workload}")
     line["gpu_launches"] = int(crys.crys_launch_count() - launches0)

@@ -118,6 +118,12 @@ __device__ __forceinline__ void bulk_load(void* dst_smem, const void* src, uint3
       : "memory");
 }
 
+// Bulk prefetch of a contiguous global range into L2 (copy engine; no registers, no
+// completion to wait for).  Address 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_prefetch_l2(const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
 // ---------------------------------------------------------------- global loads
 
 // Streaming column loads: not allocated in L1, L2 policy from policy_evict_first().

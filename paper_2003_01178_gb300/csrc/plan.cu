@@ -398,6 +398,81 @@ __device__ __forceinline__ uint32_t eval_shared(const DevQuery& q, const CachedC
   return alive;
 }
 
+// Branch-light evaluation of one query on this thread's rows for plan_kernel.  The
+// tile's columns are already on their way to L2 (bulk prefetch), so every column the
+// query reads is loaded for all rows (no selective loads and no per-group branches);
+// predicates only clear bits of the row bitmap and dead rows contribute 0.
+template <int THREADS, int ITEMS>
+__device__ __forceinline__ uint32_t eval_eager(const DevQuery& q, const GlobalCols& cols, uint32_t alive,
+                                               int32_t (&gid)[ITEMS], int64_t (&val)[ITEMS],
+                                               int32_t* err, uint64_t pol_table) {
+  constexpr int VEC = ITEMS / 4;
+  const int tid = threadIdx.x;
+  for (int f = 0; f < q.n_preds; ++f) {
+    const int c = q.pred_col[f];
+    const int32_t lo = q.pred_lo[f];
+    const uint32_t span = q.pred_span[f];
+#pragma unroll
+    for (int j = 0; j < VEC; ++j) {
+      int32_t v[4];
+      unpack4(cols.load4(c, (j * THREADS + tid) * 4), v);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) alive &= ~(static_cast<uint32_t>(!in_span(v[e], lo, span)) << (4 * j + e));
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < ITEMS; ++i) gid[i] = 0;
+  for (int jn = 0; jn < q.n_joins; ++jn) {
+    const DevJoin& J = q.joins[jn];
+    int32_t key[ITEMS], value[ITEMS];
+#pragma unroll
+    for (int j = 0; j < VEC; ++j) unpack4(cols.load4(J.fk_col, (j * THREADS + tid) * 4), key + 4 * j);
+    alive &= probe_items<ITEMS>(J.slots, J.hash, key, alive, value, pol_table);
+    for (int f = 0; f < J.n_fp; ++f) {
+      const uint32_t sh = J.fp_shift[f], mk = J.fp_mask[f], span = J.fp_span[f];
+      const int32_t lo = J.fp_lo[f];
+#pragma unroll
+      for (int i = 0; i < ITEMS; ++i)
+        alive &= ~(static_cast<uint32_t>(!in_span(field_of(value[i], sh, mk), lo, span)) << i);
+    }
+    if (J.card > 0) {
+      const uint32_t card = static_cast<uint32_t>(J.card);
+      uint32_t bad = 0;
+#pragma unroll
+      for (int i = 0; i < ITEMS; ++i) {
+        const uint32_t code = static_cast<uint32_t>(field_of(value[i], J.gshift, J.gmask));
+        bad |= static_cast<uint32_t>(code >= card) << i;
+        gid[i] += static_cast<int32_t>(code) * J.stride;
+      }
+      bad &= alive;
+      if (bad) {
+        set_error(err, CRYS_DEV_BAD_GROUP);
+        alive &= ~bad;
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < VEC; ++j) {
+    const int p = (j * THREADS + tid) * 4;
+    int32_t va[4], vb[4] = {0, 0, 0, 0};
+    unpack4(cols.load4(q.agg_a, p), va);
+    if (q.agg_op != CRYS_AGG_A) unpack4(cols.load4(q.agg_b, p), vb);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int64_t x = va[e], y = vb[e];
+      int64_t r;
+      switch (q.agg_op) {
+        case CRYS_AGG_A_MUL_B: r = x * y; break;
+        case CRYS_AGG_A_SUB_B: r = x - y; break;
+        case CRYS_AGG_A_ADD_B: r = x + y; break;
+        default: r = x; break;
+      }
+      val[4 * j + e] = ((alive >> (4 * j + e)) & 1u) ? r : 0;
+    }
+  }
+  return alive;
+}
+
 // Rows of this thread that exist in a tile with `valid` rows.
 template <int THREADS, int ITEMS>
 __device__ __forceinline__ uint32_t rows_present(int valid) {
@@ -444,7 +519,22 @@ struct PlanArgs {
   int64_t row_begin, row_end;
   DevQuery q;
   int32_t* err;
+  uint32_t col_mask;  // fact columns the query reads
 };
+
+// Thread 0 asks the copy engine to bring tile `t` of every column in `mask` into L2
+// (one bulk prefetch per column slice), so that the dependent loads of a later
+// iteration (predicate -> key -> probe -> aggregate) each wait for L2 instead of HBM.
+__device__ __forceinline__ void prefetch_tile(const int32_t* const* cols, uint32_t mask, int64_t row_begin,
+                                              int64_t t, int64_t tile, int64_t nrows) {
+  const int64_t row0 = row_begin + t * tile;
+  const int64_t valid = (nrows - t * tile) < tile ? (nrows - t * tile) : tile;
+  const uint32_t bytes = static_cast<uint32_t>(valid / 4) * 16u;
+  if (!bytes) return;
+  for (uint32_t m = mask; m; m &= m - 1) bulk_prefetch_l2(cols[__ffs(m) - 1] + row0, bytes);
+}
+
+constexpr int kPrefetchTiles = 2;  // tiles of a block prefetched ahead of the one in work
 
 template <int THREADS, int ITEMS>
 __global__ void __launch_bounds__(THREADS) plan_kernel(const __grid_constant__ PlanArgs a) {
@@ -466,7 +556,14 @@ __global__ void __launch_bounds__(THREADS) plan_kernel(const __grid_constant__ P
   const uint64_t pol = policy_evict_first();
   const uint64_t pol_table = policy_evict_last();
   const Probed none = {nullptr, nullptr};
+  if (threadIdx.x == 0)
+    for (int d = 0; d < kPrefetchTiles; ++d) {
+      const int64_t tt = blockIdx.x + static_cast<int64_t>(d) * gridDim.x;
+      if (tt < ntiles) prefetch_tile(a.cols, a.col_mask, a.row_begin, tt, TILE, nrows);
+    }
   for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int64_t ahead = t + static_cast<int64_t>(kPrefetchTiles) * gridDim.x;
+    if (threadIdx.x == 0 && ahead < ntiles) prefetch_tile(a.cols, a.col_mask, a.row_begin, ahead, TILE, nrows);
     GlobalCols cols;
     cols.pol = pol;
     cols.cols = a.cols;
@@ -474,16 +571,20 @@ __global__ void __launch_bounds__(THREADS) plan_kernel(const __grid_constant__ P
     cols.valid = static_cast<int>((nrows - t * TILE) < TILE ? (nrows - t * TILE) : TILE);
     int32_t gid[ITEMS];
     int64_t val[ITEMS];
-    const uint32_t alive = eval_query<THREADS, ITEMS>(q, cols, rows_present<THREADS, ITEMS>(cols.valid),
-                                                      none, gid, val, a.err, pol_table);
+    const uint32_t alive = q.never ? 0u
+                                   : eval_eager<THREADS, ITEMS>(q, cols, rows_present<THREADS, ITEMS>(cols.valid),
+                                                                gid, val, a.err, pol_table);
+    if (q.acc_mode == kAccSingle) {
+#pragma unroll
+      for (int i = 0; i < ITEMS; ++i) my_sum += static_cast<uint64_t>(val[i]);
+      my_count += __popc(alive);
+      continue;
+    }
     if (!alive) continue;
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
       if (!((alive >> i) & 1u)) continue;
-      if (q.acc_mode == kAccSingle) {
-        my_sum += static_cast<uint64_t>(val[i]);
-        my_count += 1;
-      } else if (q.acc_mode == kAccShared) {
+      if (q.acc_mode == kAccShared) {
         atomicAdd(acc.sums + gid[i], static_cast<unsigned long long>(val[i]));
         atomicAdd(acc.counts + gid[i], 1u);
       } else {
@@ -557,7 +658,16 @@ __global__ void __launch_bounds__(THREADS, (24 * kWarp) / THREADS > 0 ? (24 * kW
   const int64_t ntiles = (nrows + TILE - 1) / TILE;
   const uint64_t pol = policy_evict_first();
   const uint64_t pol_table = policy_evict_last();
+  uint32_t union_mask = 0;
+  for (int u = 0; u < a.n_union; ++u) union_mask |= 1u << a.union_cols[u];
+  if (tid == 0)
+    for (int d = 0; d < kPrefetchTiles; ++d) {
+      const int64_t tt = blockIdx.x + static_cast<int64_t>(d) * gridDim.x;
+      if (tt < ntiles) prefetch_tile(a.cols, union_mask, a.row_begin, tt, TILE, nrows);
+    }
   for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int64_t ahead = t + static_cast<int64_t>(kPrefetchTiles) * gridDim.x;
+    if (tid == 0 && ahead < ntiles) prefetch_tile(a.cols, union_mask, a.row_begin, ahead, TILE, nrows);
     const int64_t row0 = a.row_begin + t * TILE;
     const int valid = static_cast<int>((nrows - t * TILE) < TILE ? (nrows - t * TILE) : TILE);
     const uint32_t live = rows_present<THREADS, ITEMS>(valid);
@@ -955,6 +1065,7 @@ int crys_run_plan(const crys_table* fact, const crys_plan* plan, crys_stream str
   uint32_t mask = 0;
   if (to_device(*fact, *plan, &a.q, &mask) != CRYS_OK) return CRYS_EINVAL;
   for (int c = 0; c < fact->n_cols; ++c) a.cols[c] = fact->cols[c];
+  a.col_mask = mask;
   a.row_begin = 0;
   a.row_end = fact->n_rows;
   a.err = device_error_word();
