@@ -248,10 +248,10 @@ int crys_run_plan(const crys_table* fact, const crys_plan* plan, crys_stream s);
 
 /* Shared scan: up to CRYS_MAX_PLANS queries over rows [row_begin, row_end) of the same
  * fact table in ONE kernel: each tile of the union of the queries' columns is read from
- * HBM once (staged in shared memory by bulk asynchronous copies) and every query is
- * evaluated on it.  When the queries' joins use at most 8 distinct (fact column, table)
- * pairs, each distinct pair is probed once per row for the whole batch and the queries
- * read the probed values; otherwise every query probes its own tables.  With
+ * HBM once (bulk-prefetched into L2 a few tiles ahead, then read through L1) and every
+ * query is evaluated on it.  A (fact column, table) pair that two or more of the queries
+ * join on is probed once per row for the whole batch (the 8 most used such pairs) and
+ * those queries read the probed value; any other join is probed by its own query.  With
  * CRYS_ACCUMULATE the outputs are added to instead of overwritten, so a query can be
  * carried across several row segments (a circular scan that queries join and leave at
  * segment boundaries).  row_begin must be a multiple of 4. */
