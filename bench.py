@@ -203,6 +203,9 @@ def run_served(args, rank, world, local):
             store.run_shared(cqs)
         return qs, cqs
 
+    tune_cqs = [store.compile(q, mode="resident") for q in batch_queries(seed, 20_000, rank)]
+    tile = autotune(crys.OP_SHARED_SCAN, lambda: store.run_shared(tune_cqs), args)
+    del tune_cqs
     for w in range(args.warmup):
         one_step(10_000 + w)
     torch.cuda.synchronize(dev)
@@ -244,7 +247,8 @@ def run_served(args, rank, world, local):
                    "step": "compile 32 queries against the resident packed dimension tables + one shared "
                            "scan of the fact table (each dimension probed once per row for the batch)",
                    "l2": "inputs larger than L2 (19.2 GB fact table per scan)",
-                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "tile": tile},
         "scanned_gbs": {"aggregate": round(scanned_gbs, 1),
                         "per_query_mean_gb": round(sum(per_query_bytes) / len(per_query_bytes) / 1e9, 3),
                         "note": "sum over queries of each query's own column bytes / wall time"},
@@ -320,25 +324,38 @@ def oracle_threads():
     return oracle.hardware_threads()
 
 
-def cpu_baseline_served(store, args):
-    """The oracle (plain row-at-a-time C, rows split over all host threads) on a sample:
-    the first batch's 32 queries over the first `sample_rows` fact rows, scaled to the
-    full table."""
-    import datagen
+def oracle_query_seconds(host, query, sample_rows, full_rows, threads):
+    """Time of the oracle (as it stands) for one query over `full_rows` fact rows,
+    extrapolated from two timed runs: over 0 rows (its fixed cost: indexing the
+    dimension tables) and over the first `sample_rows` rows (t = fixed + rows * per_row)."""
     import oracle
+    t0 = time.perf_counter()
+    oracle.ss_run(host, query, threads=threads, fact_rows=0)
+    fixed = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.ss_run(host, query, threads=threads, fact_rows=sample_rows)
+    sampled = time.perf_counter() - t0
+    per_row = max(0.0, sampled - fixed) / sample_rows
+    return fixed + per_row * full_rows, fixed + sampled
+
+
+def cpu_baseline_served(store, args):
+    """The oracle (plain row-at-a-time C, rows split over all host threads) on a bounded
+    sample: a few queries of the first batch, each timed over 0 and over the first
+    `cpu_sample_rows` fact rows, extrapolated to the full table."""
     rows = min(args.cpu_sample_rows, store.n_rows)
     host = {"fact": {c: store.fact[c][:rows].cpu().numpy() for c in store.schema.fact_cols},
             "dims": {d: {k: v.cpu().numpy() for k, v in t.items()} for d, t in store.dims.items()}}
     threads = oracle_threads()
-    qs = batch_queries(args.seed, 0)
-    t0 = time.perf_counter()
+    qs = batch_queries(args.seed, 0)[: args.cpu_queries]
+    full, spent = 0.0, 0.0
     for q in qs:
-        oracle.ss_run(host, q, threads=threads)
-    dt = time.perf_counter() - t0
-    full_dt = dt * store.n_rows / rows
-    return {"value": round(BATCH / full_dt, 4), "unit": "queries/s", "cores": threads, "kind": "oracle",
-            "sample": f"32 queries of step 0 over the first {rows} of {store.n_rows} fact rows "
-                      f"({dt:.2f} s), scaled by rows"}
+        f, sp = oracle_query_seconds(host, q, rows, store.n_rows, threads)
+        full += f
+        spent += sp
+    return {"value": round(len(qs) / full, 4), "unit": "queries/s", "cores": threads, "kind": "oracle",
+            "sample": f"{len(qs)} queries of the first batch, each timed over 0 and over the first {rows} "
+                      f"of {store.n_rows} fact rows and extrapolated linearly to all rows ({spent:.1f} s spent)"}
 
 
 # ----------------------------------------------------------------------------- operators
@@ -386,6 +403,19 @@ def op_line(args, world, name, value, unit, kernel, alg_bytes, avg_ms, config, e
     return out
 
 
+def autotune(op, launch, args):
+    """Pick the tile shape of `op` on this workload (crys_tile_variants x timing) unless
+    --no-tune; returns the chosen (threads, items) and the median ms of every variant."""
+    import paper_2003_01178_gb300 as crys
+    from paper_2003_01178_gb300 import tuner
+    times = {}
+    if not args.no_tune:
+        res = tuner.tune(op, launch, reps=3, warmup=1)
+        times = {f"{v['threads']}x{v['items']}": round(v["ms"], 4) for v in res["variants"].values()}
+    v = crys.crys_get_tile(op)
+    return {"shape": list(crys.crys_tile_variants(op)[v]), "variants_ms": times}
+
+
 def time_launches(fn, steps, warmup, stream, flush=None):
     import torch
     for _ in range(warmup):
@@ -421,6 +451,8 @@ def run_operator(args, rank, world, local):
             x = dgd.uniform_i32(seed, datagen.STREAMS["sel.x"], n, 0, (1 << 31) - 1, dev)
             out = torch.empty(n, dtype=torch.int32, device=dev)
             cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+            tile = autotune(crys.OP_SELECT, lambda: crys.crys_select(x, n, -(1 << 31), datagen.select_threshold(0.5),
+                                                                      out, cnt, 0), args)
             sweep = {}
             for sigma in [i / 10 for i in range(11)]:
                 hi = datagen.select_threshold(sigma)
@@ -432,12 +464,13 @@ def run_operator(args, rank, world, local):
             line = op_line(args, world, "select", alg / (avg / 1e3) / 1e9, "GB/s", "select_kernel", alg, avg,
                            {"rows": n, "selectivity": "0.0..1.0 step 0.1 (mean over the sweep)",
                             "l2": "inputs larger than L2"},
-                           {"sweep_ms": {k: round(v, 4) for k, v in sweep.items()}})
+                           {"sweep_ms": {k: round(v, 4) for k, v in sweep.items()}, "tile": tile})
         elif args.workload == "project":
             n = args.rows or (1 << 29)
             x1 = dgd.uniform_f32(seed, datagen.STREAMS["proj.x1"], n, dev)
             x2 = dgd.uniform_f32(seed, datagen.STREAMS["proj.x2"], n, dev)
             y = torch.empty_like(x1)
+            tile = autotune(crys.OP_PROJECT, lambda: crys.crys_project(x1, x2, n, 2.0, 3.0, crys.PROJ_LINEAR, y), args)
             res = {}
             for op, nm in ((crys.PROJ_LINEAR, "linear"), (crys.PROJ_SIGMOID, "sigmoid")):
                 res[nm] = statistics.median(time_launches(
@@ -445,7 +478,7 @@ def run_operator(args, rank, world, local):
             avg = statistics.mean(res.values())
             line = op_line(args, world, "project", 12 * n / (avg / 1e3) / 1e9, "GB/s", "project_kernel", 12 * n, avg,
                            {"rows": n, "dtype": "f32", "l2": "inputs larger than L2"},
-                           {"ms": {k: round(v, 4) for k, v in res.items()}})
+                           {"ms": {k: round(v, 4) for k, v in res.items()}, "tile": tile})
         elif args.workload == "join":
             n_probe = args.rows or (1 << 28)
             fk_pay = None
@@ -459,12 +492,14 @@ def run_operator(args, rank, world, local):
                 pay = dgd.uniform_i32(seed, datagen.STREAMS["join.pay"], n_probe, 1, 100, dev) if fk_pay is None else fk_pay
                 fk_pay = pay
                 s = torch.zeros(2, dtype=torch.int64, device=dev)
+                tile = autotune(crys.OP_PROBE,
+                                lambda: crys.crys_probe_aggregate(fk, pay, n_probe, ht.struct, s[0:1], s[1:2]), args)
                 ms = time_launches(lambda: crys.crys_probe_aggregate(fk, pay, n_probe, ht.struct, s[0:1], s[1:2]),
                                    args.steps, args.warmup, stream)
                 bms = time_launches(lambda: (crys.crys_hash_init(ht.struct), crys.crys_hash_build(bk, bv, nb, [], ht.struct)),
                                     max(1, args.steps // 2), 1, stream)
                 res[f"2^{lg}"] = {"probe_ms": round(statistics.median(ms), 4), "build_ms": round(statistics.median(bms), 4),
-                                  "table_mb": round(ht.nbytes / 2 ** 20, 3)}
+                                  "table_mb": round(ht.nbytes / 2 ** 20, 3), "tile": tile}
                 del ht, bk, bv, fk
             # headline: the largest table (HBM-resident probes)
             last = res[f"2^{args.join_sizes[-1]}"]
@@ -480,13 +515,15 @@ def run_operator(args, rank, world, local):
             ko, vo = torch.empty_like(keys), torch.empty_like(vals)
             tb = crys.crys_sort(None, None, None, None, n, None, -1)
             temp = crys.scratch(tb, dev)
+            tile = autotune(crys.OP_SORT, lambda: crys.crys_sort(keys, vals, ko, vo, n, temp, tb), args)
             ms = time_launches(lambda: crys.crys_sort(keys, vals, ko, vo, n, temp, tb), args.steps, args.warmup, stream)
             avg = statistics.median(ms)
             line = op_line(args, world, "sort", n / (avg / 1e3) / 1e6, "Mkeys/s", "sort_pass_kernel", 68 * n, avg,
-                           {"rows": n, "l2": "inputs larger than L2", "passes": "4 x 8-bit, stable"})
+                           {"rows": n, "l2": "inputs larger than L2", "passes": "4 x 8-bit, stable"},
+                           {"tile": tile})
         elif args.workload == "q1":
             sizes = [args.rows] if args.rows else [1 << 22, 1 << 28]
-            results = {}
+            results, tiles = {}, {}
             flush_buf = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
             for n in sizes:
                 t = dgd.q1_tables(seed, n, dev)
@@ -496,14 +533,17 @@ def run_operator(args, rank, world, local):
                 cnts = torch.zeros(1, dtype=torch.int64, device=dev)
                 table = crys.make_table([f["fk"], f["a"], f["b"], f["c"]])
                 plan = crys.make_plan([(1, -(1 << 31), 24), (2, 1, 3)], [(0, ht, 0)], ("mul", 3, 2), sums, cnts)
+                tile = autotune(crys.OP_PLAN, lambda: (l2_flush(flush_buf), crys.crys_run_plan(table, plan)), args)
                 ms = time_launches(lambda: crys.crys_run_plan(table, plan), args.steps, args.warmup, stream,
                                    flush=lambda: l2_flush(flush_buf))
                 results[n] = statistics.median(ms)
+                tiles[n] = tile
                 del t, f, d, ht, table, plan
             n = sizes[0]
             avg = results[n]
             extra = {"by_rows": {str(k): {"ms": round(v, 4), "GB/s": round(16 * k / (v / 1e3) / 1e9, 1),
-                                          "frac": round(16 * k / (v / 1e3) / 1e9 / measured_hbm_peak()[0], 4)}
+                                          "frac": round(16 * k / (v / 1e3) / 1e9 / measured_hbm_peak()[0], 4),
+                                          "tile": tiles[k]}
                                  for k, v in results.items()}}
             line = op_line(args, world, "q1", 16 * n / (avg / 1e3) / 1e9, "GB/s", "plan_kernel", 16 * n, avg,
                            {"rows": n, "dtype": "int64", "l2": "flushed between timed launches (512 MB write)",
@@ -520,7 +560,9 @@ def run_operator(args, rank, world, local):
 
 def run_reference(args, rank, world):
     """The oracle as it stands, on the host cores, on a bounded sample of each step's
-    workload, scaled to the same unit as our arm."""
+    workload (a few of the step's queries, each timed over 0 and over the first
+    `cpu_sample_rows` fact rows and extrapolated to the full table), reported in our
+    arm's unit."""
     if rank != 0:
         return None
     import datagen
@@ -531,26 +573,27 @@ def run_reference(args, rank, world):
         raise SystemExit("--impl reference is implemented for the served workload")
     rows = min(args.cpu_sample_rows, args.rows)
     host = datagen.ss_tables(args.seed, rows, dim_scale=args.dim_scale)
-    times = []
+    full_s, spent, nq = 0.0, 0.0, 0
     for s in range(args.warmup + args.steps):
-        qs = batch_queries(args.seed, s)
-        t0 = time.perf_counter()
+        qs = batch_queries(args.seed, s)[: args.cpu_queries]
         for q in qs:
-            oracle.ss_run(host, q, threads=threads)
-        dt = time.perf_counter() - t0
-        if s >= args.warmup:
-            times.append(dt * args.rows / rows)
-    total = sum(times)
-    qps = BATCH * args.steps / total
+            f, sp = oracle_query_seconds(host, q, rows, args.rows, threads)
+            if s >= args.warmup:
+                full_s += f
+                spent += sp
+                nq += 1
+    qps = nq / full_s
     return {"metric": METRIC, "value": round(qps, 4), "unit": "queries/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total / args.steps * 1e3, 3),
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(full_s / args.steps * 1e3, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
             "data": "synthetic (seeded counter-based generator)", "impl": "reference",
-            "config": {"workload": "served star-schema stream (see our arm)", "fact_rows": args.rows,
-                       "batch_queries": BATCH},
+            "config": {"workload": "served star-schema stream: fact 600M rows x 8 int32 cols, dims "
+                                   "2556/200K/3M/1.4M rows, seeded select-join-group-by queries",
+                       "fact_rows": args.rows, "batch_queries": BATCH},
             "cpu_baseline": {"value": round(qps, 4), "unit": "queries/s", "cores": threads, "kind": "oracle",
-                             "sample": f"each step: 32 queries over the first {rows} fact rows, time scaled "
-                                       f"to {args.rows} rows"},
+                             "sample": f"each step: {args.cpu_queries} of the step's queries, each timed over 0 "
+                                       f"and over the first {rows} fact rows, extrapolated to {args.rows} rows "
+                                       f"({spent:.1f} s spent in timed steps)"},
             "e2e": {"value": round(qps, 4), "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -568,10 +611,12 @@ def main():
     p.add_argument("--seed", type=int, default=0xC0FFEE + 4)
     p.add_argument("--segments", type=int, default=8)
     p.add_argument("--served-queries", type=int, default=512)
-    p.add_argument("--cpu-sample-rows", type=int, default=6_000_000)
+    p.add_argument("--cpu-sample-rows", type=int, default=2_000_000)
+    p.add_argument("--cpu-queries", type=int, default=4, help="queries per step timed on the CPU")
     p.add_argument("--join-sizes", type=int, nargs="+", default=[10, 14, 18, 20, 22, 24, 26, 27])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--quick", action="store_true", help="skip the one-at-a-time and served-loop legs")
+    p.add_argument("--no-tune", action="store_true", help="keep the default tile shapes")
     args = p.parse_args()
     if args.warmup < 3:
         raise SystemExit("at least 3 warm-up steps")

@@ -114,21 +114,28 @@ int crys_project(const float* x1, const float* x2, int64_t n, float a, float b, 
 /* ------------------------------------------------------------------ hash join
  * Section 4.3: no-partitioning hash join over a linear-probing table that is a plain
  * array of 8-byte slots (no pointers).  Slot = key in the low 32 bits, value in the high
- * 32 bits; an empty slot is all ones, so key -1 cannot be stored.  capacity is a power of
- * two; the paper's tables run at 50% fill, i.e. capacity = 2 * rows.  Home slot of key k:
- *   CRYS_HASH_MULT  (0, default) multiplicative (Fibonacci) hashing,
- *                   (uint32)(k * 2654435769) >> (32 - log2(capacity));
- *   CRYS_HASH_IDENT (1) k mod capacity: perfect hashing when the keys are dense
- *                   (0..n-1 with capacity >= n, as for star-schema dimension keys; the
- *                   paper's Section 5.3 cost model assumes perfect hashing), so a table
- *                   needs only capacity >= n and every probe reads one slot;
- * then linear probing with wrap-around. */
+ * 32 bits; an empty slot is all ones, so key -1 cannot be stored.  The paper's tables run
+ * at 50% fill, i.e. capacity = 2 * rows.  Home slot of key k:
+ *   CRYS_HASH_MULT   (0, default) multiplicative (Fibonacci) hashing,
+ *                    (uint32)(k * 2654435769) >> (32 - log2(capacity));
+ *   CRYS_HASH_IDENT  (1) k mod capacity: perfect hashing when the keys are dense
+ *                    (0..n-1 with capacity >= n, as for star-schema dimension keys; the
+ *                    paper's Section 5.3 cost model assumes perfect hashing), so a table
+ *                    needs only capacity >= n and every probe reads one slot;
+ * then linear probing with wrap-around (capacity a power of two, >= 2); or
+ *   CRYS_HASH_DIRECT (2) slot k holds key k: every key must lie in [0, capacity) (the
+ *                    build flags CRYS_DEV_BAD_KEY otherwise), capacity is any value >= 1
+ *                    (no power of two needed: n dense keys need exactly n slots), and a
+ *                    lookup reads one slot, or none for a key outside [0, capacity).
+ *                    Direct tables also let a shared scan tag dimension rows with query
+ *                    bitmaps (crys_run_plans_tagged). */
 #define CRYS_HASH_MULT 0
 #define CRYS_HASH_IDENT 1
+#define CRYS_HASH_DIRECT 2
 typedef struct {
-  uint64_t* slots;  /* capacity slots (device), caller-owned */
-  int64_t capacity; /* power of two, >= 2 */
-  int32_t kind;     /* CRYS_HASH_MULT or CRYS_HASH_IDENT */
+  uint64_t* slots;  /* capacity slots (device), caller-owned, 8-byte aligned */
+  int64_t capacity; /* <= 2^31; a power of two >= 2 unless CRYS_HASH_DIRECT */
+  int32_t kind;     /* CRYS_HASH_MULT, CRYS_HASH_IDENT or CRYS_HASH_DIRECT */
 } crys_hash;
 
 /* Conjunctive range predicate on a device column: lo <= col[row] <= hi. */
@@ -258,6 +265,26 @@ int crys_run_plan(const crys_table* fact, const crys_plan* plan, crys_stream s);
 #define CRYS_ACCUMULATE 0x1
 int crys_run_plans(const crys_table* fact, const crys_plan* plans, int32_t n_plans,
                    int64_t row_begin, int64_t row_end, int flags, crys_stream s);
+
+/* Shared scan with query bitmaps: the shared join of CJOIN (Candea, Polyzotis and
+ * Vingralek, VLDB 2009) applied to one batch.  When every join of every plan is on a
+ * CRYS_HASH_DIRECT table (at most 8 distinct (fact column, table) pairs), each pair gets
+ * a per-batch array of `capacity` 8-byte entries: the slot's value in the high word and,
+ * in the low word, the bitmap of the batch's plans that the dimension row satisfies (bit
+ * q set when plan q does not join through the pair, or joins it and the row passes all
+ * of q's bit-field predicates on it).  The fact scan ANDs one entry per pair into each
+ * row's bitmap and finishes only the (row, plan) pairs still set: fact predicates, group
+ * code, aggregate.  Results are those of crys_run_plans, and so is every argument rule.
+ *   crys_run_plans_tagged_bytes  scratch bytes the bitmaps of this batch need; 0 when the
+ *                                batch cannot be tagged.
+ *   scratch       device memory, 16-byte aligned, rebuilt by every call.  With scratch
+ *                 NULL or smaller than needed, or a batch that cannot be tagged, the call
+ *                 runs crys_run_plans instead (same results, no bitmaps). */
+int crys_run_plans_tagged_bytes(const crys_table* fact, const crys_plan* plans, int32_t n_plans,
+                                int64_t* bytes);
+int crys_run_plans_tagged(const crys_table* fact, const crys_plan* plans, int32_t n_plans,
+                          int64_t row_begin, int64_t row_end, int flags, void* scratch,
+                          int64_t scratch_bytes, crys_stream s);
 
 /* ------------------------------------------------------------------ tile shapes
  * Each operator is compiled for several tile shapes (threads per block x items per

@@ -27,7 +27,7 @@ AGG_A, AGG_A_MUL_B, AGG_A_SUB_B, AGG_A_ADD_B = 0, 1, 2, 3
 AGG_OPS = {"sum": AGG_A, "mul": AGG_A_MUL_B, "sub": AGG_A_SUB_B, "add": AGG_A_ADD_B}
 MAX_COLS, MAX_PREDS, MAX_JOINS, MAX_PLANS, MAX_FIELD_PREDS = 16, 8, 4, 32, 2
 ACCUMULATE = 1
-HASH_MULT, HASH_IDENT = 0, 1
+HASH_MULT, HASH_IDENT, HASH_DIRECT = 0, 1, 2
 OP_SELECT, OP_PROJECT, OP_PROBE, OP_PLAN, OP_SHARED_SCAN, OP_SORT = range(6)
 OP_NAMES = ["select", "project", "probe", "plan", "shared_scan", "sort"]
 
@@ -102,13 +102,18 @@ def lib():
         L.crys_run_plan.argtypes = [C.POINTER(crys_table), C.POINTER(crys_plan), p]
         L.crys_run_plans.argtypes = [C.POINTER(crys_table), C.POINTER(crys_plan), i32, i64, i64,
                                      C.c_int, p]
+        L.crys_run_plans_tagged_bytes.argtypes = [C.POINTER(crys_table), C.POINTER(crys_plan), i32,
+                                                  C.POINTER(C.c_int64)]
+        L.crys_run_plans_tagged.argtypes = [C.POINTER(crys_table), C.POINTER(crys_plan), i32, i64, i64,
+                                            C.c_int, p, i64, p]
         L.crys_tile_variants.argtypes = [C.c_int, C.POINTER(C.c_int32), C.POINTER(C.c_int32), i32]
         L.crys_set_tile.argtypes = [C.c_int, i32]
         L.crys_get_tile.argtypes = [C.c_int]
         for fn in ("crys_device_errors", "crys_select", "crys_select_static", "crys_project", "crys_hash_init",
                    "crys_hash_build", "crys_probe_aggregate", "crys_sort", "crys_plan_groups",
                    "crys_pack_fields",
-                   "crys_run_plan", "crys_run_plans", "crys_tile_variants", "crys_set_tile",
+                   "crys_run_plan", "crys_run_plans", "crys_run_plans_tagged_bytes",
+                   "crys_run_plans_tagged", "crys_tile_variants", "crys_set_tile",
                    "crys_get_tile"):
             getattr(L, fn).restype = C.c_int
         _lib = L
@@ -230,6 +235,23 @@ def crys_run_plans(fact: crys_table, plans, row_begin: int, row_end: int, flags:
                                 _stream(stream)), "crys_run_plans")
 
 
+def crys_run_plans_tagged_bytes(fact: crys_table, plans) -> int:
+    """Scratch bytes of the query bitmaps of a batch; 0 when it cannot be tagged."""
+    arr = (crys_plan * max(1, len(plans)))(*plans)
+    out = C.c_int64(0)
+    _check(lib().crys_run_plans_tagged_bytes(C.byref(fact), arr, len(plans), C.byref(out)),
+           "crys_run_plans_tagged_bytes")
+    return out.value
+
+
+def crys_run_plans_tagged(fact: crys_table, plans, row_begin: int, row_end: int, flags: int = 0,
+                          scratch=None, scratch_bytes: int = 0, stream=None) -> None:
+    arr = (crys_plan * max(1, len(plans)))(*plans)
+    _check(lib().crys_run_plans_tagged(C.byref(fact), arr, len(plans), row_begin, row_end, flags,
+                                       _ptr(scratch), scratch_bytes, _stream(stream)),
+           "crys_run_plans_tagged")
+
+
 def crys_tile_variants(op: int) -> list:
     t = (C.c_int32 * 16)()
     i = (C.c_int32 * 16)()
@@ -289,8 +311,11 @@ def project(x1: torch.Tensor, x2: torch.Tensor, a: float = 2.0, b: float = 3.0, 
 
 
 def capacity_for(rows: int, kind: int = 0) -> int:
-    """Power-of-two capacity for `rows` keys: at most 50% fill for multiplicative
-    hashing; at least `rows` slots for identity hashing of dense keys."""
+    """Capacity for `rows` keys: a power of two at most 50% full for multiplicative
+    hashing; a power of two of at least `rows` slots for identity hashing of dense keys;
+    exactly `rows` slots for a direct table of the keys 0..rows-1."""
+    if kind == HASH_DIRECT:
+        return max(1, rows)
     need = 2 * rows if kind == HASH_MULT else rows
     cap = 2
     while cap < need:
@@ -299,10 +324,13 @@ def capacity_for(rows: int, kind: int = 0) -> int:
 
 
 class HashTable:
-    """A device linear-probing table (caller-owned slot array) and its crys_hash view."""
+    """A device hash table (caller-owned slot array) and its crys_hash view."""
 
     def __init__(self, capacity: int, device, kind: int = HASH_MULT):
-        if capacity < 2 or capacity & (capacity - 1):
+        if kind == HASH_DIRECT:
+            if capacity < 1:
+                raise ValueError("a direct table needs capacity >= 1")
+        elif capacity < 2 or capacity & (capacity - 1):
             raise ValueError("capacity must be a power of two >= 2")
         self.slots = torch.empty(capacity, dtype=torch.int64, device=device)
         self.capacity = capacity

@@ -175,11 +175,27 @@ __device__ __forceinline__ void st_relaxed_u32(uint32_t* p, uint32_t v) {
 // hashing (key mod capacity) uses mult = 1, shift = 0.
 struct HashFn {
   uint32_t mult, shift, mask;
+  uint32_t limit;  // keys >= limit (as unsigned) are absent without reading a slot
+  uint32_t steps;  // further slots a lookup may examine after the home slot
 };
 
-__host__ __device__ __forceinline__ HashFn make_hash(int32_t kind, uint32_t log2cap) {
+// Hash function of a table kind and capacity (a power of two except for direct tables).
+__host__ __device__ __forceinline__ HashFn make_hash(int32_t kind, int64_t capacity) {
   HashFn h;
+  if (kind == CRYS_HASH_DIRECT) {
+    // the slot of key k is k itself: a key is in its slot or absent
+    h.mult = 1u;
+    h.shift = 0u;
+    h.mask = 0xFFFFFFFFu;
+    h.limit = static_cast<uint32_t>(capacity);
+    h.steps = 0u;
+    return h;
+  }
+  uint32_t log2cap = 0;
+  while ((int64_t{1} << log2cap) < capacity) ++log2cap;
   h.mask = (log2cap >= 32) ? 0xFFFFFFFFu : ((1u << log2cap) - 1u);
+  h.limit = 0xFFFFFFFFu;  // key -1 is the empty marker and never stored
+  h.steps = h.mask;
   if (kind == CRYS_HASH_IDENT) {
     h.mult = 1u;
     h.shift = 0u;
@@ -194,36 +210,34 @@ __device__ __forceinline__ uint32_t hash_slot(int32_t key, const HashFn& f) {
   return ((static_cast<uint32_t>(key) * f.mult) >> f.shift) & f.mask;
 }
 
-// Looks `key` up by linear probing; returns the value, or false when absent.
-__device__ __forceinline__ bool hash_find(const uint64_t* slots, const HashFn& f, int32_t key,
-                                          int32_t* value, uint64_t pol) {
-  uint32_t h = hash_slot(key, f);
-  for (uint32_t probe = 0; probe <= f.mask; ++probe) {
-    uint64_t s = ld_slot(slots + h, pol);
-    if (s == kEmptySlot) return false;
-    if (static_cast<uint32_t>(s) == static_cast<uint32_t>(key)) {
-      *value = static_cast<int32_t>(s >> 32);
-      return true;
-    }
-    h = (h + 1) & f.mask;
-  }
-  return false;
+// Whether a key can be in the table at all (direct tables: 0 <= key < capacity).
+__device__ __forceinline__ bool hash_may_hold(int32_t key, const HashFn& f) {
+  return static_cast<uint32_t>(key) < f.limit;
 }
 
-// Continues a probe whose first slot `s` (at index h) was already loaded.
-__device__ __forceinline__ bool hash_resolve(const uint64_t* slots, uint32_t mask, uint32_t h,
+// Continues a lookup whose home slot `s` (at index h) was already loaded (kEmptySlot when
+// the key cannot be in the table): linear probing until the key or an empty slot.
+__device__ __forceinline__ bool hash_resolve(const uint64_t* slots, const HashFn& f, uint32_t h,
                                              uint64_t s, int32_t key, int32_t* value,
                                              uint64_t pol) {
-  for (uint32_t probe = 0; probe <= mask; ++probe) {
+  for (uint32_t probe = 0;; ++probe) {
     if (s == kEmptySlot) return false;
     if (static_cast<uint32_t>(s) == static_cast<uint32_t>(key)) {
       *value = static_cast<int32_t>(s >> 32);
       return true;
     }
-    h = (h + 1) & mask;
+    if (probe >= f.steps) return false;
+    h = (h + 1) & f.mask;
     s = ld_slot(slots + h, pol);
   }
-  return false;
+}
+
+// Looks `key` up; returns the value, or false when absent.
+__device__ __forceinline__ bool hash_find(const uint64_t* slots, const HashFn& f, int32_t key,
+                                          int32_t* value, uint64_t pol) {
+  if (!hash_may_hold(key, f)) return false;
+  const uint32_t h = hash_slot(key, f);
+  return hash_resolve(slots, f, h, ld_slot(slots + h, pol), key, value, pol);
 }
 
 // ---------------------------------------------------------------- scans / reductions

@@ -42,7 +42,7 @@ __global__ void __launch_bounds__(256) build_kernel(const __grid_constant__ Buil
     if (!keep) continue;
     const int32_t key = a.keys[i];
     const int32_t val = a.vals ? a.vals[i] : 0;
-    if (key == -1) {
+    if (key == -1 || !hash_may_hold(key, a.hash)) {  // reserved, or outside a direct table
       set_error(a.err, CRYS_DEV_BAD_KEY);
       continue;
     }
@@ -50,7 +50,7 @@ __global__ void __launch_bounds__(256) build_kernel(const __grid_constant__ Buil
                             (static_cast<uint64_t>(static_cast<uint32_t>(val)) << 32);
     uint32_t h = hash_slot(key, a.hash);
     bool placed = false;
-    for (uint32_t probe = 0; probe <= a.hash.mask; ++probe) {
+    for (uint32_t probe = 0; probe <= a.hash.steps; ++probe) {
       uint64_t cur = a.slots[h];
       if (cur == kEmptySlot) {
         cur = atomicCAS(reinterpret_cast<unsigned long long*>(a.slots + h), kEmptySlot, packed);
@@ -151,12 +151,13 @@ __global__ void __launch_bounds__(THREADS) probe_kernel(ProbeArgs a) {
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
       h[i] = hash_slot(key[i], a.hash);
-      slot[i] = (live >> i) & 1u ? ld_slot(a.slots + h[i], pol_table) : kEmptySlot;
+      slot[i] = ((live >> i) & 1u) && hash_may_hold(key[i], a.hash) ? ld_slot(a.slots + h[i], pol_table)
+                                                                      : kEmptySlot;
     }
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
       int32_t value;
-      if (((live >> i) & 1u) && hash_resolve(a.slots, a.hash.mask, h[i], slot[i], key[i], &value, pol_table)) {
+      if (((live >> i) & 1u) && hash_resolve(a.slots, a.hash, h[i], slot[i], key[i], &value, pol_table)) {
         sum += static_cast<uint64_t>(static_cast<int64_t>(pay[i]) * static_cast<int64_t>(value));
         matches += 1;
       }
@@ -193,9 +194,11 @@ int launch_probe(ProbeArgs a, cudaStream_t s) {
 }
 
 bool valid_table(const crys_hash* ht) {
-  return ht && ht->slots && is_pow2(ht->capacity) && ht->capacity >= 2 &&
-         ht->capacity <= (1ll << 31) && (reinterpret_cast<uintptr_t>(ht->slots) & 7u) == 0 &&
-         (ht->kind == CRYS_HASH_MULT || ht->kind == CRYS_HASH_IDENT);
+  if (!ht || !ht->slots || (reinterpret_cast<uintptr_t>(ht->slots) & 7u) != 0 || ht->capacity > (1ll << 31))
+    return false;
+  if (ht->kind == CRYS_HASH_DIRECT) return ht->capacity >= 1;
+  return (ht->kind == CRYS_HASH_MULT || ht->kind == CRYS_HASH_IDENT) && is_pow2(ht->capacity) &&
+         ht->capacity >= 2;
 }
 
 int grid_for(int64_t n, int threads) {
@@ -239,7 +242,7 @@ int crys_hash_build(const int32_t* keys, const int32_t* vals, int64_t n, const c
     a.filters[f] = filters[f];
   }
   a.slots = ht->slots;
-  a.hash = make_hash(ht->kind, log2_pow2(static_cast<uint64_t>(ht->capacity)));
+  a.hash = make_hash(ht->kind, ht->capacity);
   a.err = device_error_word();
   if (!a.err) return CRYS_ECUDA;
   build_kernel<<<grid_for(n, 256), 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(a);
@@ -261,7 +264,7 @@ int crys_probe_aggregate(const int32_t* fk, const int32_t* payload, int64_t n, c
   a.pay = payload;
   a.n = n;
   a.slots = ht->slots;
-  a.hash = make_hash(ht->kind, log2_pow2(static_cast<uint64_t>(ht->capacity)));
+  a.hash = make_hash(ht->kind, ht->capacity);
   a.sum = reinterpret_cast<unsigned long long*>(d_sum);
   a.matches = reinterpret_cast<unsigned long long*>(d_matches);
   a.err = device_error_word();

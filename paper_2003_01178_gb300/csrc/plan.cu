@@ -1,20 +1,19 @@
 // Fused select-join-aggregate pipelines (Section 5.3; Figure "tile-extension"): after
 // the dimension tables are built, ONE kernel streams the fact table in tiles and, per
-// tile, applies the fact predicates (BlockPred), loads later columns only for rows still
-// alive (BlockLoadSel: a 16-byte group is fetched only if one of its rows is alive), probes
-// the dimension tables (BlockLookup), checks the dimension predicates on bit fields of
-// the joined values, forms the group id and accumulates SUM(expr) and COUNT per group
-// (BlockAggregate into per-block partials, flushed with one atomic per non-empty group
-// and block).
+// tile, applies the fact predicates (BlockPred), probes the dimension tables
+// (BlockLookup), checks the dimension predicates on bit fields of the joined values,
+// forms the group id and accumulates SUM(expr) and COUNT per group (BlockAggregate into
+// per-block partials, flushed with one atomic per non-empty group and block).
 //
-// Two kernels share the per-query evaluation:
-//  * plan_kernel        one query; columns read straight from global memory so that
-//                       BlockLoadSel saves sectors of dead rows.
-//  * shared_scan_kernel up to 32 queries over the same fact table; the union of their
-//                       columns is staged per tile in shared memory by bulk copies, so
-//                       each fact tile crosses HBM once however many queries read it,
-//                       and each distinct (foreign key, table) pair of the batch is
-//                       probed once per row for all queries that join through it.
+// Kernels:
+//  * plan_kernel        one query.  The copy engine prefetches each tile's columns into
+//                       L2 a few tiles ahead (bulk prefetch), and the evaluation is
+//                       branch-light: every column the query reads is loaded for every
+//                       row and predicates only clear bits of a row bitmap.
+//  * shared_scan_kernel up to 32 queries over the same fact table: each tile of the
+//                       union of their columns crosses HBM once, and each (foreign
+//                       key, table) pair that several queries join through is probed
+//                       once per row for all of them.
 #include "common.cuh"
 #include "pipeline.cuh"
 #include "tiles.h"
@@ -110,36 +109,6 @@ struct CachedCols {
   }
 };
 
-// Column access from the shared-memory stage (shared_scan_kernel).
-struct StagedCols {
-  const int32_t* const* cols;
-  const int32_t* slot_of;  // table column -> staged slice
-  const int32_t* stage;
-  int tile;
-  int64_t row0;
-  int valid, bulk;
-  __device__ __forceinline__ int4 load4(int c, int p) const {
-    return stage_read4(stage + slot_of[c] * tile, cols[c] + row0, p, bulk, valid);
-  }
-  // One value of column c (staged in slice `slot`) at tile row r < valid.
-  __device__ __forceinline__ int32_t value(int slot, int c, int r) const {
-    return r < bulk ? stage[slot * tile + r] : cols[c][row0 + r];
-  }
-  // Column c known to be staged in slice `slot`.
-  __device__ __forceinline__ int4 load4s(int slot, int c, int p) const {
-    const int32_t* st = stage + slot * tile;
-    if (p + 4 <= bulk) return *reinterpret_cast<const int4*>(st + p);
-    return stage_read4(st, cols[c] + row0, p, bulk, valid);
-  }
-};
-
-// Values probed once per batch: value of item i of thread t for probe d at
-// values[(d * ITEMS + i) * THREADS + t]; found bits at found[d * THREADS + t].
-struct Probed {
-  const int32_t* values;
-  const uint32_t* found;
-};
-
 __device__ __forceinline__ void unpack4(int4 q, int32_t* dst) {
   dst[0] = q.x;
   dst[1] = q.y;
@@ -153,115 +122,21 @@ template <int ITEMS>
 __device__ __forceinline__ uint32_t probe_items(const uint64_t* slots, const HashFn& hf,
                                                 const int32_t (&key)[ITEMS], uint32_t live,
                                                 int32_t (&value)[ITEMS], uint64_t pol) {
-  const uint32_t mask = hf.mask;
   uint32_t h[ITEMS];
   uint64_t slot[ITEMS];
 #pragma unroll
   for (int i = 0; i < ITEMS; ++i) {
     h[i] = hash_slot(key[i], hf);
-    slot[i] = ((live >> i) & 1u) ? ld_slot(slots + h[i], pol) : kEmptySlot;
+    slot[i] = ((live >> i) & 1u) && hash_may_hold(key[i], hf) ? ld_slot(slots + h[i], pol) : kEmptySlot;
   }
   uint32_t found = 0;
 #pragma unroll
   for (int i = 0; i < ITEMS; ++i) {
     value[i] = 0;
-    if (((live >> i) & 1u) && hash_resolve(slots, mask, h[i], slot[i], key[i], &value[i], pol))
+    if (((live >> i) & 1u) && hash_resolve(slots, hf, h[i], slot[i], key[i], &value[i], pol))
       found |= 1u << i;
   }
   return found;
-}
-
-// Evaluates one query on this thread's ITEMS rows of a tile (4-row groups
-// j*THREADS + tid).  Returns the bitmap of rows that qualify; gid/val hold their group
-// id and aggregate value.
-template <int THREADS, int ITEMS, typename Cols>
-__device__ __forceinline__ uint32_t eval_query(const DevQuery& q, const Cols& cols, uint32_t alive,
-                                               const Probed& probed, int32_t (&gid)[ITEMS],
-                                               int64_t (&val)[ITEMS], int32_t* err,
-                                               uint64_t pol_table) {
-  constexpr int VEC = ITEMS / 4;
-  const int tid = threadIdx.x;
-  // BlockPred over the fact predicates, each column read only for live groups.
-  for (int f = 0; f < q.n_preds && alive; ++f) {
-    const int c = q.pred_col[f];
-    const int32_t lo = q.pred_lo[f], hi = q.pred_hi[f];
-#pragma unroll
-    for (int j = 0; j < VEC; ++j) {
-      if ((alive >> (4 * j)) & 0xFu) {
-        int32_t v[4];
-        unpack4(cols.load4(c, (j * THREADS + tid) * 4), v);
-#pragma unroll
-        for (int e = 0; e < 4; ++e)
-          if (v[e] < lo || v[e] > hi) alive &= ~(1u << (4 * j + e));
-      }
-    }
-  }
-#pragma unroll
-  for (int i = 0; i < ITEMS; ++i) gid[i] = 0;
-  // BlockLookup into each dimension table (or read the batch-wide probe results).
-  for (int jn = 0; jn < q.n_joins && alive; ++jn) {
-    const DevJoin& J = q.joins[jn];
-    int32_t value[ITEMS];
-    if (J.probe >= 0) {
-      alive &= probed.found[J.probe * THREADS + tid];
-#pragma unroll
-      for (int i = 0; i < ITEMS; ++i) value[i] = probed.values[(J.probe * ITEMS + i) * THREADS + tid];
-    } else {
-      int32_t key[ITEMS];
-#pragma unroll
-      for (int j = 0; j < VEC; ++j) {
-        if ((alive >> (4 * j)) & 0xFu)
-          unpack4(cols.load4(J.fk_col, (j * THREADS + tid) * 4), key + 4 * j);
-        else
-          key[4 * j] = key[4 * j + 1] = key[4 * j + 2] = key[4 * j + 3] = 0;
-      }
-      alive &= probe_items<ITEMS>(J.slots, J.hash, key, alive, value, pol_table);
-    }
-    for (int f = 0; f < J.n_fp; ++f) {
-      const uint32_t sh = J.fp_shift[f], mk = J.fp_mask[f];
-      const int32_t lo = J.fp_lo[f], hi = J.fp_hi[f];
-#pragma unroll
-      for (int i = 0; i < ITEMS; ++i) {
-        const int32_t fv = field_of(value[i], sh, mk);
-        if (fv < lo || fv > hi) alive &= ~(1u << i);
-      }
-    }
-    if (J.card > 0) {
-      const uint32_t card = static_cast<uint32_t>(J.card);
-#pragma unroll
-      for (int i = 0; i < ITEMS; ++i) {
-        const uint32_t code = static_cast<uint32_t>(field_of(value[i], J.gshift, J.gmask));
-        if (((alive >> i) & 1u) && code >= card) {
-          set_error(err, CRYS_DEV_BAD_GROUP);
-          alive &= ~(1u << i);
-        }
-        gid[i] += static_cast<int32_t>(code) * J.stride;
-      }
-    }
-  }
-  if (!alive) return 0;
-  // BlockLoadSel of the aggregate operands and the expression in int64.
-#pragma unroll
-  for (int j = 0; j < VEC; ++j) {
-    if (!((alive >> (4 * j)) & 0xFu)) continue;
-    const int p = (j * THREADS + tid) * 4;
-    int32_t va[4], vb[4] = {0, 0, 0, 0};
-    unpack4(cols.load4(q.agg_a, p), va);
-    if (q.agg_op != CRYS_AGG_A) unpack4(cols.load4(q.agg_b, p), vb);
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const int64_t x = va[e], y = vb[e];
-      int64_t r;
-      switch (q.agg_op) {
-        case CRYS_AGG_A_MUL_B: r = x * y; break;
-        case CRYS_AGG_A_SUB_B: r = x - y; break;
-        case CRYS_AGG_A_ADD_B: r = x + y; break;
-        default: r = x; break;
-      }
-      val[4 * j + e] = r;
-    }
-  }
-  return alive;
 }
 
 // Range test lo <= v <= hi as one unsigned comparison (span = hi - lo).
@@ -555,7 +430,6 @@ __global__ void __launch_bounds__(THREADS) plan_kernel(const __grid_constant__ P
   uint64_t my_sum = 0, my_count = 0;
   const uint64_t pol = policy_evict_first();
   const uint64_t pol_table = policy_evict_last();
-  const Probed none = {nullptr, nullptr};
   if (threadIdx.x == 0)
     for (int d = 0; d < kPrefetchTiles; ++d) {
       const int64_t tt = blockIdx.x + static_cast<int64_t>(d) * gridDim.x;
@@ -692,7 +566,9 @@ __global__ void __launch_bounds__(THREADS, (24 * kWarp) / THREADS > 0 ? (24 * kW
 #pragma unroll
         for (int i = 0; i < ITEMS; ++i) {
           h[dd][i] = hash_slot(key[dd][i], P.hash);
-          slot[dd][i] = ((live >> i) & 1u) ? ld_slot(P.slots + h[dd][i], pol_table) : kEmptySlot;
+          slot[dd][i] = ((live >> i) & 1u) && hash_may_hold(key[dd][i], P.hash)
+                            ? ld_slot(P.slots + h[dd][i], pol_table)
+                            : kEmptySlot;
         }
       }
 #pragma unroll
@@ -706,7 +582,7 @@ __global__ void __launch_bounds__(THREADS, (24 * kWarp) / THREADS > 0 ? (24 * kW
         for (int i = 0; i < ITEMS; ++i) {
           value[i] = 0;
           if (((live >> i) & 1u) &&
-              hash_resolve(P.slots, P.hash.mask, h[dd][i], slot[dd][i], key[dd][i], &value[i], pol_table))
+              hash_resolve(P.slots, P.hash, h[dd][i], slot[dd][i], key[dd][i], &value[i], pol_table))
             found |= 1u << i;
         }
         pf[d * THREADS + tid] = found;
@@ -762,6 +638,277 @@ __global__ void __launch_bounds__(THREADS, (24 * kWarp) / THREADS > 0 ? (24 * kW
   }
 }
 
+// ------------------------------------------------------------------ tagged shared scan
+//
+// Query bitmaps over direct dimension tables (the shared join of CJOIN, Candea et al.,
+// VLDB 2009, applied to one batch of a shared scan).  For every distinct (fact column,
+// table) pair of the batch, annotate_kernel writes one 8-byte entry per table slot:
+// the slot's value in the high word and, in the low word, the bitmap of the batch's
+// queries the dimension row satisfies (bit q set when query q does not join through the
+// pair, or joins it and the row passes all of q's bit-field predicates on it).  The
+// fact scan then needs one lookup per pair and row to know every query's dimension
+// verdict at once: the AND of the entries' bitmaps.  Only the (row, query) pairs left
+// set are expanded, compacted per warp and finished one pair per lane (fact predicates,
+// group code, aggregate), so a query costs in proportion to the rows it keeps.
+
+constexpr int kMaxTagPairs = 8;
+constexpr int kMaxTagEntries = CRYS_MAX_PLANS * CRYS_MAX_JOINS;
+// Words of a query's descriptor in shared memory; odd, so that lanes reading the same
+// field of different queries fall in different banks.
+constexpr int kDescWords = 61;
+enum DescField : int {
+  kDPreds = 0,        // number of fact predicates
+  kDPredCol = 1,      // 8 columns
+  kDPredLo = 9,       // 8 lower bounds
+  kDPredSpan = 17,    // 8 spans (hi - lo)
+  kDGroups = 25,      // grouped joins
+  kDGPair = 26,       // 4 pair indexes
+  kDGShift = 30,      // 4
+  kDGMask = 34,       // 4
+  kDGCard = 38,       // 4
+  kDGStride = 42,     // 4
+  kDAggOp = 46,
+  kDAggA = 47,
+  kDAggB = 48,
+  kDAccMode = 49,
+  kDAccOff = 50,
+  kDSums = 51,        // 2 words
+  kDCounts = 53,      // 2 words
+};
+
+struct TagPair {
+  const uint64_t* slots;  // the direct table
+  uint64_t* ann;          // per-batch entries, one per slot
+  uint32_t limit;         // capacity
+  int32_t fk_col;
+  uint32_t nonjoin;       // queries that do not join through the pair
+  uint32_t join;          // queries that do
+  int32_t first_entry, n_entries;
+};
+
+struct TagEntry {  // one join of one query through a pair
+  int32_t q;
+  int32_t n_fp;
+  uint32_t fp_shift[CRYS_MAX_FIELD_PREDS], fp_mask[CRYS_MAX_FIELD_PREDS], fp_span[CRYS_MAX_FIELD_PREDS];
+  int32_t fp_lo[CRYS_MAX_FIELD_PREDS];
+};
+
+struct AnnotateArgs {
+  int32_t n_pairs;
+  TagPair pairs[kMaxTagPairs];
+  TagEntry entries[kMaxTagEntries];
+};
+
+__global__ void __launch_bounds__(256) annotate_kernel(const __grid_constant__ AnnotateArgs a) {
+  const TagPair& P = a.pairs[blockIdx.y];
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < P.limit; i += stride) {
+    const uint64_t s = P.slots[i];
+    const int32_t v = static_cast<int32_t>(s >> 32);
+    uint32_t bits = P.nonjoin;
+    if (s != kEmptySlot) {
+      uint32_t fail = 0;
+      for (int e = P.first_entry; e < P.first_entry + P.n_entries; ++e) {
+        const TagEntry& E = a.entries[e];
+        bool ok = true;
+        for (int f = 0; f < E.n_fp; ++f)
+          ok = ok && in_span(field_of(v, E.fp_shift[f], E.fp_mask[f]), E.fp_lo[f], E.fp_span[f]);
+        if (!ok) fail |= 1u << E.q;
+      }
+      bits |= P.join & ~fail;
+    }
+    P.ann[i] = (static_cast<uint64_t>(static_cast<uint32_t>(v)) << 32) | bits;
+  }
+}
+
+struct TagScanPair {
+  const uint64_t* ann;
+  uint32_t limit;
+  int32_t fk_col;
+  uint32_t nonjoin;
+};
+
+struct TagArgs {
+  const int32_t* cols[CRYS_MAX_COLS];
+  uint32_t col_mask;  // fact columns the batch reads
+  int64_t row_begin, row_end;
+  int32_t n_pairs;
+  int32_t n_queries;
+  uint32_t all_mask;  // queries that can qualify at all
+  int32_t shared_groups;
+  int32_t* err;
+  TagScanPair pairs[kMaxTagPairs];
+  int32_t desc[CRYS_MAX_PLANS * kDescWords];
+};
+
+// Finishes one (row, query) pair whose dimension verdicts all passed: fact predicates,
+// group code from the pairs' values, aggregate, accumulation.
+template <int TILE>
+__device__ __forceinline__ void finish_pair(const int32_t* D, const int32_t* const* cols, int64_t grow, int r,
+                                            const int32_t* pv, const SharedAcc& acc, int32_t* err) {
+  const int32_t agg_op = D[kDAggOp];
+  const int32_t xa = ld_cached(cols[D[kDAggA]] + grow);
+  const int32_t xb = agg_op != CRYS_AGG_A ? ld_cached(cols[D[kDAggB]] + grow) : 0;
+  const int np = D[kDPreds];
+  if (np > 0) {
+    const int32_t x0 = ld_cached(cols[D[kDPredCol]] + grow);
+    const int32_t x1 = np > 1 ? ld_cached(cols[D[kDPredCol + 1]] + grow) : D[kDPredLo + 1];
+    if (!in_span(x0, D[kDPredLo], static_cast<uint32_t>(D[kDPredSpan]))) return;
+    if (!in_span(x1, D[kDPredLo + 1], static_cast<uint32_t>(D[kDPredSpan + 1]))) return;
+    for (int f = 2; f < np; ++f)
+      if (!in_span(ld_cached(cols[D[kDPredCol + f]] + grow), D[kDPredLo + f],
+                   static_cast<uint32_t>(D[kDPredSpan + f])))
+        return;
+  }
+  int32_t gid = 0;
+  const int ng = D[kDGroups];
+  for (int g = 0; g < ng; ++g) {
+    const int32_t v = pv[D[kDGPair + g] * TILE + r];
+    const uint32_t code = (static_cast<uint32_t>(v) >> D[kDGShift + g]) & static_cast<uint32_t>(D[kDGMask + g]);
+    if (code >= static_cast<uint32_t>(D[kDGCard + g])) {
+      set_error(err, CRYS_DEV_BAD_GROUP);
+      return;
+    }
+    gid += static_cast<int32_t>(code) * D[kDGStride + g];
+  }
+  const int64_t x = xa, y = xb;
+  int64_t val;
+  switch (agg_op) {
+    case CRYS_AGG_A_MUL_B: val = x * y; break;
+    case CRYS_AGG_A_SUB_B: val = x - y; break;
+    case CRYS_AGG_A_ADD_B: val = x + y; break;
+    default: val = x; break;
+  }
+  if (D[kDAccMode] != kAccGlobal) {
+    const int slot = D[kDAccOff] + gid;
+    atomicAdd(acc.sums + slot, static_cast<unsigned long long>(val));
+    atomicAdd(acc.counts + slot, 1u);
+  } else {
+    unsigned long long* sums = reinterpret_cast<unsigned long long*>(
+        (static_cast<uint64_t>(static_cast<uint32_t>(D[kDSums + 1])) << 32) | static_cast<uint32_t>(D[kDSums]));
+    unsigned long long* counts = reinterpret_cast<unsigned long long*>(
+        (static_cast<uint64_t>(static_cast<uint32_t>(D[kDCounts + 1])) << 32) | static_cast<uint32_t>(D[kDCounts]));
+    atomicAdd(sums + gid, static_cast<unsigned long long>(val));
+    if (counts) atomicAdd(counts + gid, 1ull);
+  }
+}
+
+// Shared memory of a block: query descriptors, the fact column pointers, the pairs'
+// values of the tile's rows (pv[p * TILE + r]), one (row, query) list per warp, then the
+// group accumulators.
+template <int THREADS, int ITEMS>
+struct TagSmem {
+  static constexpr int TILE = THREADS * ITEMS;
+  static constexpr int LIST = kWarp * CRYS_MAX_PLANS;  // one row per lane, every query
+  static constexpr size_t desc_bytes = CRYS_MAX_PLANS * kDescWords * 4;
+  static constexpr size_t cols_off = (desc_bytes + 15) / 16 * 16;
+  static constexpr size_t pv_off = cols_off + CRYS_MAX_COLS * 8;
+  __host__ __device__ static size_t list_off(int n_pairs) { return pv_off + static_cast<size_t>(n_pairs) * TILE * 4; }
+  __host__ __device__ static size_t acc_off(int n_pairs) { return list_off(n_pairs) + static_cast<size_t>(THREADS / kWarp) * LIST * 2; }
+};
+
+template <int THREADS, int ITEMS>
+__global__ void __launch_bounds__(THREADS, (24 * kWarp) / THREADS > 0 ? (24 * kWarp) / THREADS : 1)
+    tagged_scan_kernel(const __grid_constant__ TagArgs a) {
+  using L = TagSmem<THREADS, ITEMS>;
+  constexpr int TILE = L::TILE;
+  constexpr int VEC = ITEMS / 4;
+  static_assert(TILE <= 2048, "a list entry holds an 11-bit tile row");
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const int tid = threadIdx.x, lane = tid % kWarp, warp = tid / kWarp;
+  int32_t* desc = reinterpret_cast<int32_t*>(smem_raw);
+  const int32_t** scols = reinterpret_cast<const int32_t**>(smem_raw + L::cols_off);
+  int32_t* pv = reinterpret_cast<int32_t*>(smem_raw + L::pv_off);
+  uint16_t* list = reinterpret_cast<uint16_t*>(smem_raw + L::list_off(a.n_pairs)) + warp * L::LIST;
+  const SharedAcc acc = shared_acc(smem_raw + L::acc_off(a.n_pairs), a.shared_groups);
+  for (int w = tid; w < a.n_queries * kDescWords; w += THREADS) desc[w] = a.desc[w];
+  if (tid < CRYS_MAX_COLS) scols[tid] = a.cols[tid];
+  for (int g = tid; g < a.shared_groups; g += THREADS) {
+    acc.sums[g] = 0;
+    acc.counts[g] = 0;
+  }
+  __syncthreads();
+
+  const int64_t nrows = a.row_end - a.row_begin;
+  const int64_t ntiles = (nrows + TILE - 1) / TILE;
+  const uint64_t pol = policy_evict_first();
+  const uint64_t pol_table = policy_evict_last();
+  if (tid == 0)
+    for (int d = 0; d < kPrefetchTiles; ++d) {
+      const int64_t tt = blockIdx.x + static_cast<int64_t>(d) * gridDim.x;
+      if (tt < ntiles) prefetch_tile(a.cols, a.col_mask, a.row_begin, tt, TILE, nrows);
+    }
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int64_t ahead = t + static_cast<int64_t>(kPrefetchTiles) * gridDim.x;
+    if (tid == 0 && ahead < ntiles) prefetch_tile(a.cols, a.col_mask, a.row_begin, ahead, TILE, nrows);
+    const int64_t row0 = a.row_begin + t * TILE;
+    const int valid = static_cast<int>((nrows - t * TILE) < TILE ? (nrows - t * TILE) : TILE);
+    const uint32_t live = rows_present<THREADS, ITEMS>(valid);
+    GlobalCols fk_cols;
+    fk_cols.cols = a.cols;
+    fk_cols.row0 = row0;
+    fk_cols.valid = valid;
+    fk_cols.pol = pol;
+    uint32_t rm[ITEMS];
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) rm[i] = ((live >> i) & 1u) ? a.all_mask : 0u;
+    __syncwarp();  // the warp is done with the previous tile's values
+    // one lookup per pair and row: AND of the dimension verdicts, values kept for groups
+    for (int p = 0; p < a.n_pairs; ++p) {
+      const TagScanPair& P = a.pairs[p];
+      int32_t key[ITEMS];
+#pragma unroll
+      for (int j = 0; j < VEC; ++j) unpack4(fk_cols.load4(P.fk_col, (j * THREADS + tid) * 4), key + 4 * j);
+      uint64_t e[ITEMS];
+#pragma unroll
+      for (int i = 0; i < ITEMS; ++i)
+        e[i] = (rm[i] && static_cast<uint32_t>(key[i]) < P.limit) ? ld_slot(P.ann + key[i], pol_table)
+                                                                  : static_cast<uint64_t>(P.nonjoin);
+#pragma unroll
+      for (int j = 0; j < VEC; ++j) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) rm[4 * j + k] &= static_cast<uint32_t>(e[4 * j + k]);
+        *reinterpret_cast<int4*>(pv + p * TILE + (j * THREADS + tid) * 4) =
+            make_int4(static_cast<int32_t>(e[4 * j] >> 32), static_cast<int32_t>(e[4 * j + 1] >> 32),
+                      static_cast<int32_t>(e[4 * j + 2] >> 32), static_cast<int32_t>(e[4 * j + 3] >> 32));
+      }
+    }
+    __syncwarp();  // values of the warp's rows visible to all its lanes
+    // per item slot: expand each lane's (row, query) pairs into the warp's list, finish them
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+      const int n = __popc(rm[i]);
+      const int incl = warp_inclusive_scan(n, lane);
+      const int total = __shfl_sync(0xFFFFFFFFu, incl, kWarp - 1);
+      if (total == 0) continue;
+      const int r = ((i >> 2) * THREADS + tid) * 4 + (i & 3);
+      int k = incl - n;
+      for (uint32_t m = rm[i]; m; m &= m - 1) list[k++] = static_cast<uint16_t>(((__ffs(m) - 1) << 11) | r);
+      __syncwarp();
+      for (int base = 0; base < total; base += kWarp) {
+        if (base + lane < total) {
+          const uint32_t ent = list[base + lane];
+          const int rr = static_cast<int>(ent & 0x7FFu);
+          finish_pair<TILE>(desc + (ent >> 11) * kDescWords, scols, row0 + rr, rr, pv, acc, a.err);
+        }
+      }
+      __syncwarp();  // the list is reused by the next item slot
+    }
+  }
+  __syncthreads();
+  for (int qi = 0; qi < a.n_queries; ++qi) {
+    const int32_t* D = desc + qi * kDescWords;
+    if (D[kDAccMode] == kAccGlobal) continue;
+    unsigned long long* sums = reinterpret_cast<unsigned long long*>(
+        (static_cast<uint64_t>(static_cast<uint32_t>(D[kDSums + 1])) << 32) | static_cast<uint32_t>(D[kDSums]));
+    unsigned long long* counts = reinterpret_cast<unsigned long long*>(
+        (static_cast<uint64_t>(static_cast<uint32_t>(D[kDCounts + 1])) << 32) | static_cast<uint32_t>(D[kDCounts]));
+    int64_t groups = 1;
+    for (int g = 0; g < D[kDGroups]; ++g) groups *= D[kDGCard + g];
+    flush_shared<THREADS>(acc, D[kDAccOff], groups, sums, counts);
+  }
+}
+
 // ------------------------------------------------------------------ packing
 
 struct PackArgs {
@@ -813,6 +960,12 @@ int groups_of(const crys_plan& p, int64_t* groups) {
   return CRYS_OK;
 }
 
+bool table_ok(const crys_hash& h) {
+  if (!h.slots || (reinterpret_cast<uintptr_t>(h.slots) & 7u) != 0 || h.capacity > (1ll << 31)) return false;
+  if (h.kind == CRYS_HASH_DIRECT) return h.capacity >= 1;
+  return (h.kind == CRYS_HASH_MULT || h.kind == CRYS_HASH_IDENT) && is_pow2(h.capacity) && h.capacity >= 2;
+}
+
 int to_device(const crys_table& t, const crys_plan& p, DevQuery* d, uint32_t* col_mask) {
   int64_t groups = 0;
   if (groups_of(p, &groups) != CRYS_OK) return CRYS_EINVAL;
@@ -839,13 +992,11 @@ int to_device(const crys_table& t, const crys_plan& p, DevQuery* d, uint32_t* co
   for (int j = 0; j < p.n_joins; ++j) {
     const crys_join& J = p.joins[j];
     DevJoin& D = d->joins[j];
-    if (!col_ok(J.fk_col) || !J.ht.slots || !is_pow2(J.ht.capacity) || J.ht.capacity < 2 ||
-        J.ht.capacity > (1ll << 31) || (J.ht.kind != CRYS_HASH_MULT && J.ht.kind != CRYS_HASH_IDENT))
-      return CRYS_EINVAL;
+    if (!col_ok(J.fk_col) || !table_ok(J.ht)) return CRYS_EINVAL;
     if (!field_ok(J.group_shift, J.group_bits) || J.n_preds < 0 || J.n_preds > CRYS_MAX_FIELD_PREDS)
       return CRYS_EINVAL;
     D.slots = J.ht.slots;
-    D.hash = make_hash(J.ht.kind, log2_pow2(static_cast<uint64_t>(J.ht.capacity)));
+    D.hash = make_hash(J.ht.kind, J.ht.capacity);
     D.fk_col = J.fk_col;
     D.card = J.group_card;
     D.stride = 0;
@@ -982,7 +1133,7 @@ void assign_probes(ScanArgs& a) {
   Pair pairs[CRYS_MAX_PLANS * CRYS_MAX_JOINS];
   int n = 0;
   auto same = [](const ProbeSpec& p, const DevJoin& J) {
-    return p.slots == J.slots && p.fk_col == J.fk_col && p.hash.mask == J.hash.mask &&
+    return p.slots == J.slots && p.fk_col == J.fk_col && p.hash.mask == J.hash.mask && p.hash.limit == J.hash.limit &&
            p.hash.mult == J.hash.mult;
   };
   for (int qi = 0; qi < a.n_queries; ++qi) {
@@ -1016,6 +1167,178 @@ void assign_probes(ScanArgs& a) {
       for (int d = 0; d < m; ++d)
         if (same(a.probes[d], a.q[qi].joins[j])) a.q[qi].joins[j].probe = d;
   a.n_probes = m;
+}
+
+// Tagging a batch: the distinct (fact column, direct table) pairs, their annotation
+// entries, the scratch layout and the per-query descriptors.  Returns false when the
+// batch cannot be tagged (a join on a table that is not direct, or too many pairs).
+struct TagBatch {
+  AnnotateArgs ann;
+  TagArgs scan;
+  int64_t bytes;   // scratch the annotations need
+  int64_t max_slots;
+};
+
+bool tag_batch(const crys_plan* plans, const DevQuery* q, int n, TagBatch* tb) {
+  AnnotateArgs& A = tb->ann;
+  TagArgs& S = tb->scan;
+  A.n_pairs = 0;
+  int pair_of[CRYS_MAX_PLANS][CRYS_MAX_JOINS];
+  for (int qi = 0; qi < n; ++qi) {
+    for (int j = 0; j < plans[qi].n_joins; ++j) {
+      const crys_join& J = plans[qi].joins[j];
+      if (J.ht.kind != CRYS_HASH_DIRECT) return false;
+      int found = -1;
+      for (int p = 0; p < A.n_pairs && found < 0; ++p)
+        if (A.pairs[p].slots == J.ht.slots && A.pairs[p].fk_col == J.fk_col &&
+            A.pairs[p].limit == static_cast<uint32_t>(J.ht.capacity))
+          found = p;
+      if (found < 0) {
+        if (A.n_pairs == kMaxTagPairs) return false;
+        found = A.n_pairs++;
+        TagPair& P = A.pairs[found];
+        P.slots = J.ht.slots;
+        P.ann = nullptr;
+        P.limit = static_cast<uint32_t>(J.ht.capacity);
+        P.fk_col = J.fk_col;
+        P.join = 0;
+        P.n_entries = 0;
+      }
+      pair_of[qi][j] = found;
+      A.pairs[found].join |= 1u << qi;
+      A.pairs[found].n_entries += 1;
+    }
+  }
+  // entries grouped by pair
+  int next[kMaxTagPairs];
+  int first = 0;
+  for (int p = 0; p < A.n_pairs; ++p) {
+    A.pairs[p].first_entry = first;
+    next[p] = first;
+    first += A.pairs[p].n_entries;
+  }
+  const uint32_t everyone = n == 32 ? 0xFFFFFFFFu : ((1u << n) - 1u);
+  for (int qi = 0; qi < n; ++qi)
+    for (int j = 0; j < q[qi].n_joins; ++j) {
+      const DevJoin& J = q[qi].joins[j];
+      TagEntry& E = A.entries[next[pair_of[qi][j]]++];
+      E.q = qi;
+      E.n_fp = J.n_fp;
+      for (int f = 0; f < CRYS_MAX_FIELD_PREDS; ++f) {
+        E.fp_shift[f] = f < J.n_fp ? J.fp_shift[f] : 0;
+        E.fp_mask[f] = f < J.n_fp ? J.fp_mask[f] : 0;
+        E.fp_lo[f] = f < J.n_fp ? J.fp_lo[f] : 0;
+        E.fp_span[f] = f < J.n_fp ? J.fp_span[f] : 0;
+      }
+    }
+  tb->bytes = 0;
+  tb->max_slots = 0;
+  S.n_pairs = A.n_pairs;
+  for (int p = 0; p < A.n_pairs; ++p) {
+    TagPair& P = A.pairs[p];
+    P.nonjoin = everyone & ~P.join;
+    S.pairs[p].limit = P.limit;
+    S.pairs[p].fk_col = P.fk_col;
+    S.pairs[p].nonjoin = P.nonjoin;
+    tb->bytes += (static_cast<int64_t>(P.limit) * 8 + 15) / 16 * 16;
+    if (P.limit > tb->max_slots) tb->max_slots = P.limit;
+  }
+  // descriptors
+  S.n_queries = n;
+  S.all_mask = 0;
+  for (int w = 0; w < CRYS_MAX_PLANS * kDescWords; ++w) S.desc[w] = 0;
+  for (int qi = 0; qi < n; ++qi) {
+    const DevQuery& Q = q[qi];
+    int32_t* D = S.desc + qi * kDescWords;
+    if (!Q.never) S.all_mask |= 1u << qi;
+    D[kDPreds] = Q.n_preds;
+    for (int f = 0; f < Q.n_preds; ++f) {
+      D[kDPredCol + f] = Q.pred_col[f];
+      D[kDPredLo + f] = Q.pred_lo[f];
+      D[kDPredSpan + f] = static_cast<int32_t>(Q.pred_span[f]);
+    }
+    int ng = 0;
+    for (int j = 0; j < Q.n_joins; ++j) {
+      const DevJoin& J = Q.joins[j];
+      if (J.card <= 0) continue;
+      D[kDGPair + ng] = pair_of[qi][j];
+      D[kDGShift + ng] = static_cast<int32_t>(J.gshift);
+      D[kDGMask + ng] = static_cast<int32_t>(J.gmask);
+      D[kDGCard + ng] = J.card;
+      D[kDGStride + ng] = J.stride;
+      ++ng;
+    }
+    D[kDGroups] = ng;
+    D[kDAggOp] = Q.agg_op;
+    D[kDAggA] = Q.agg_a;
+    D[kDAggB] = Q.agg_b;
+    const uint64_t sp = reinterpret_cast<uint64_t>(Q.sums), cp = reinterpret_cast<uint64_t>(Q.counts);
+    D[kDSums] = static_cast<int32_t>(static_cast<uint32_t>(sp));
+    D[kDSums + 1] = static_cast<int32_t>(static_cast<uint32_t>(sp >> 32));
+    D[kDCounts] = static_cast<int32_t>(static_cast<uint32_t>(cp));
+    D[kDCounts + 1] = static_cast<int32_t>(static_cast<uint32_t>(cp >> 32));
+  }
+  return true;
+}
+
+// Places the annotations in scratch and launches the annotation and the scan.
+template <int THREADS, int ITEMS>
+int launch_tagged(TagBatch& tb, const DevQuery* q, unsigned char* scratch, cudaStream_t s) {
+  using L = TagSmem<THREADS, ITEMS>;
+  constexpr int TILE = L::TILE;
+  AnnotateArgs& A = tb.ann;
+  TagArgs& S = tb.scan;
+  int64_t off = 0;
+  for (int p = 0; p < A.n_pairs; ++p) {
+    A.pairs[p].ann = reinterpret_cast<uint64_t*>(scratch + off);
+    S.pairs[p].ann = A.pairs[p].ann;
+    off += (static_cast<int64_t>(A.pairs[p].limit) * 8 + 15) / 16 * 16;
+  }
+  if (A.n_pairs > 0) {
+    int64_t gx = (tb.max_slots + 255) / 256;
+    const int64_t cap = static_cast<int64_t>(sm_count()) * 8;
+    if (gx > cap) gx = cap;
+    annotate_kernel<<<dim3(static_cast<unsigned>(gx < 1 ? 1 : gx), static_cast<unsigned>(A.n_pairs)), 256, 0, s>>>(A);
+    note_launch();
+    const int rc = check_launch();
+    if (rc != CRYS_OK) return rc;
+  }
+  // Group accumulators in shared memory for as many queries as fit next to the fixed
+  // parts (smallest group counts first); the rest accumulate with global atomics.
+  const size_t fixed = L::acc_off(S.n_pairs);
+  const size_t share = (220u * 1024u) / kScanBlocksPerSM;
+  const size_t budget = share > fixed ? share - fixed : 0;
+  int order[CRYS_MAX_PLANS];
+  for (int qi = 0; qi < S.n_queries; ++qi) order[qi] = qi;
+  for (int i = 1; i < S.n_queries; ++i)
+    for (int j = i; j > 0 && q[order[j]].groups < q[order[j - 1]].groups; --j) {
+      const int t = order[j];
+      order[j] = order[j - 1];
+      order[j - 1] = t;
+    }
+  int64_t used = 0;
+  for (int oi = 0; oi < S.n_queries; ++oi) {
+    const int qi = order[oi];
+    int32_t* D = S.desc + qi * kDescWords;
+    if (static_cast<size_t>(used + q[qi].groups) * 12 <= budget) {
+      D[kDAccMode] = kAccShared;
+      D[kDAccOff] = static_cast<int32_t>(used);
+      used += q[qi].groups;
+    } else {
+      D[kDAccMode] = kAccGlobal;
+      D[kDAccOff] = 0;
+    }
+  }
+  S.shared_groups = static_cast<int32_t>(used);
+  const size_t smem = fixed + static_cast<size_t>(used) * 12;
+  auto k = tagged_scan_kernel<THREADS, ITEMS>;
+  if (!allow_smem(k, smem)) return CRYS_ECUDA;
+  const int64_t ntiles = (S.row_end - S.row_begin + TILE - 1) / TILE;
+  const int grid = persistent_grid(k, THREADS, smem, ntiles);
+  if (!counts_fit(S.row_end - S.row_begin, grid)) return CRYS_EINVAL;
+  k<<<grid, THREADS, smem, s>>>(S);
+  note_launch();
+  return check_launch();
 }
 
 }  // namespace
@@ -1163,6 +1486,74 @@ int crys_run_plans(const crys_table* fact, const crys_plan* plans, int32_t n_pla
     }
   }
   delete a;
+  return rc;
+}
+
+int crys_run_plans_tagged_bytes(const crys_table* fact, const crys_plan* plans, int32_t n_plans,
+                                int64_t* bytes) {
+  using namespace crys;
+  if (!bytes || check_table(fact) != CRYS_OK || n_plans < 0 || n_plans > CRYS_MAX_PLANS) return CRYS_EINVAL;
+  if (n_plans > 0 && !plans) return CRYS_EINVAL;
+  *bytes = 0;
+  DevQuery* q = new DevQuery[CRYS_MAX_PLANS]();
+  TagBatch* tb = new TagBatch();
+  int rc = CRYS_OK;
+  for (int qi = 0; qi < n_plans && rc == CRYS_OK; ++qi) {
+    uint32_t m = 0;
+    rc = to_device(*fact, plans[qi], &q[qi], &m);
+  }
+  if (rc == CRYS_OK && tag_batch(plans, q, n_plans, tb)) *bytes = tb->bytes;
+  delete tb;
+  delete[] q;
+  return rc;
+}
+
+int crys_run_plans_tagged(const crys_table* fact, const crys_plan* plans, int32_t n_plans,
+                          int64_t row_begin, int64_t row_end, int flags, void* scratch,
+                          int64_t scratch_bytes, crys_stream stream) {
+  using namespace crys;
+  if (check_table(fact) != CRYS_OK || n_plans < 0 || n_plans > CRYS_MAX_PLANS) return CRYS_EINVAL;
+  if (n_plans > 0 && !plans) return CRYS_EINVAL;
+  if (row_begin < 0 || row_end < row_begin || row_end > fact->n_rows || (row_begin & 3)) return CRYS_EINVAL;
+  if (flags & ~CRYS_ACCUMULATE) return CRYS_EINVAL;
+  if (scratch_bytes < 0 || (scratch && !aligned16(scratch))) return CRYS_EINVAL;
+  DevQuery* q = new DevQuery[CRYS_MAX_PLANS]();
+  TagBatch* tb = new TagBatch();
+  uint32_t mask = 0;
+  int rc = CRYS_OK;
+  for (int qi = 0; qi < n_plans && rc == CRYS_OK; ++qi) {
+    uint32_t m = 0;
+    rc = to_device(*fact, plans[qi], &q[qi], &m);
+    mask |= m;
+  }
+  const bool tagged = rc == CRYS_OK && tag_batch(plans, q, n_plans, tb) && scratch && tb->bytes <= scratch_bytes;
+  if (rc == CRYS_OK && !tagged) {
+    delete tb;
+    delete[] q;
+    return crys_run_plans(fact, plans, n_plans, row_begin, row_end, flags, stream);
+  }
+  TagArgs& S = tb->scan;
+  for (int c = 0; c < CRYS_MAX_COLS; ++c) S.cols[c] = c < fact->n_cols ? fact->cols[c] : nullptr;
+  S.col_mask = mask;
+  S.row_begin = row_begin;
+  S.row_end = row_end;
+  S.err = device_error_word();
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (rc == CRYS_OK && !S.err) rc = CRYS_ECUDA;
+  if (rc == CRYS_OK && !(flags & CRYS_ACCUMULATE))
+    for (int qi = 0; qi < n_plans && rc == CRYS_OK; ++qi) rc = zero_outputs(q[qi], s);
+  if (rc == CRYS_OK && n_plans > 0 && row_end > row_begin) {
+    unsigned char* base = static_cast<unsigned char*>(scratch);
+    constexpr int kOp = CRYS_OP_SHARED_SCAN;
+    switch (tile_variant(kOp)) {
+      case 1: rc = launch_tagged<kTiles[kOp][1].threads, kTiles[kOp][1].items>(*tb, q, base, s); break;
+      case 2: rc = launch_tagged<kTiles[kOp][2].threads, kTiles[kOp][2].items>(*tb, q, base, s); break;
+      case 3: rc = launch_tagged<kTiles[kOp][3].threads, kTiles[kOp][3].items>(*tb, q, base, s); break;
+      default: rc = launch_tagged<kTiles[kOp][0].threads, kTiles[kOp][0].items>(*tb, q, base, s); break;
+    }
+  }
+  delete tb;
+  delete[] q;
   return rc;
 }
 

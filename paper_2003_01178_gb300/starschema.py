@@ -9,12 +9,13 @@ group attribute per dimension, one SUM expression) compiles to one of two plan s
   expected selectivity with an 8-sigma margin; a full table is flagged on the device and
   ``check_device_errors`` raises, so a wrong estimate never goes unnoticed.
 * ``mode="resident"`` — every dimension has one resident table, built when the schema is
-  loaded (identity-hashed, the paper's "perfect hashing" of dense dimension keys, so the
-  four tables total about 50 MB and stay in L2), whose value packs all of the dimension's
-  attribute codes into bit fields; a
-  query's dimension filters and group attribute become bit-field predicates and a
-  bit-field group code on that shared table, so a query needs no build at all and a
-  shared scan probes each dimension once per row for the whole batch.
+  loaded (a direct table: the slot of key k is k, the paper's "perfect hashing" of dense
+  dimension keys, so the four tables total about 37 MB and stay in L2), whose value packs
+  all of the dimension's attribute codes into bit fields; a query's dimension filters and
+  group attribute become bit-field predicates and a bit-field group code on that shared
+  table, so a query needs no build at all.  A shared scan of such queries tags every
+  dimension row with the bitmap of the batch's queries it satisfies and reads one tag
+  per dimension and fact row (``crys_run_plans_tagged``).
 
 Both shapes give identical results (integer sums and counts per group).
 """
@@ -26,8 +27,8 @@ from dataclasses import dataclass, field
 import torch
 
 from . import (HashTable, crys_hash_build, crys_hash_init, crys_pack_fields, crys_run_plan,
-               crys_run_plans, make_plan, make_table, capacity_for, ACCUMULATE, MAX_PLANS,
-               HASH_IDENT)
+               crys_run_plans_tagged, crys_run_plans_tagged_bytes, make_plan, make_table,
+               capacity_for, ACCUMULATE, MAX_PLANS, HASH_DIRECT, HASH_IDENT)
 
 
 @dataclass
@@ -85,10 +86,17 @@ class ResidentStarSchema:
                              [fields[a][1] for a in names], rows, packed, stream)
             self.fields[d] = fields
             self.packed[d] = packed
-            # dimension keys are dense, so the resident table uses identity hashing
-            # (perfect hashing: capacity >= rows, one slot per probe); other key sets
-            # still work, with linear probing resolving collisions
-            self.resident[d] = HashTable.build(dim["key"], packed, stream=stream, kind=HASH_IDENT)
+            # Dimension keys are dense (0..rows-1, shuffled), so the resident table is a
+            # direct table: slot k holds key k.  Other key sets fall back to identity
+            # hashing with linear probing.
+            keys = dim["key"]
+            lo, hi = (int(keys.min().item()), int(keys.max().item())) if rows else (0, 0)
+            if rows and lo >= 0 and hi < (1 << 31):
+                self.resident[d] = HashTable.build(keys, packed, capacity=hi + 1, stream=stream,
+                                                   kind=HASH_DIRECT)
+            else:
+                self.resident[d] = HashTable.build(keys, packed, stream=stream, kind=HASH_IDENT)
+        self._scratch = None                          # query bitmaps of the latest shared scan
 
     @property
     def resident_bytes(self) -> int:
@@ -163,12 +171,18 @@ class ResidentStarSchema:
 
     def run_shared(self, cqs: list, row_begin: int = 0, row_end: int | None = None,
                    accumulate: bool = False, stream=None) -> None:
-        """Up to 32 queries in one shared scan over rows [row_begin, row_end)."""
+        """Up to 32 queries in one shared scan over rows [row_begin, row_end); with the
+        resident direct tables the batch is tagged with query bitmaps."""
         if len(cqs) > MAX_PLANS:
             raise ValueError("at most 32 queries per shared scan")
         row_end = self.n_rows if row_end is None else row_end
-        crys_run_plans(self.table, [c.plan for c in cqs], row_begin, row_end,
-                       ACCUMULATE if accumulate else 0, stream)
+        plans = [c.plan for c in cqs]
+        need = crys_run_plans_tagged_bytes(self.table, plans)
+        if need and (self._scratch is None or self._scratch.numel() < need):
+            self._scratch = torch.empty(need, dtype=torch.uint8, device=self.device)
+        scratch = self._scratch if need else None
+        crys_run_plans_tagged(self.table, plans, row_begin, row_end, ACCUMULATE if accumulate else 0,
+                              scratch, scratch.numel() if need else 0, stream)
 
     def query_columns(self, query: dict) -> set:
         cols = {c for (c, _, _) in query["fact_preds"]}

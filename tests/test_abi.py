@@ -94,3 +94,43 @@ def test_product_does_not_import_oracle():
             "paper_2003_01178_gb300.starschema, paper_2003_01178_gb300.server; "
             "assert 'oracle' not in sys.modules, 'oracle imported'" % ROOT)
     subprocess.check_call([sys.executable, "-c", code])
+
+
+def test_tagged_scan_scratch_sizing(crys):
+    """Host-side sizing of the query bitmaps (no device access): one entry of 8 bytes per
+    slot of each distinct (fact column, direct table) pair, 16-byte rounded; 0 when a
+    join is on a table of another kind."""
+    L = crys.lib()
+    t = crys.crys_table()
+    t.n_cols = 3
+    t.n_rows = 1000
+    for c in range(3):
+        t.cols[c] = 4096 * (c + 1)
+
+    def plan(fk, slots, cap, kind):
+        p = crys.crys_plan()
+        p.n_joins = 1
+        p.joins[0].fk_col = fk
+        p.joins[0].ht = crys.crys_hash(C.c_void_p(slots), cap, kind)
+        p.agg_a = 2
+        p.d_sums = 1 << 20
+        return p
+
+    D = crys.HASH_DIRECT
+    plans = [plan(0, 1 << 16, 1001, D), plan(0, 1 << 16, 1001, D), plan(1, 1 << 24, 7, D)]
+    arr = (crys.crys_plan * 3)(*plans)
+    b = C.c_int64(-1)
+    assert L.crys_run_plans_tagged_bytes(C.byref(t), arr, 3, C.byref(b)) == crys.OK
+    assert b.value == (1001 * 8 + 15) // 16 * 16 + (7 * 8 + 15) // 16 * 16
+    plans[2] = plan(1, 1 << 24, 8, crys.HASH_MULT)
+    arr = (crys.crys_plan * 3)(*plans)
+    assert L.crys_run_plans_tagged_bytes(C.byref(t), arr, 3, C.byref(b)) == crys.OK and b.value == 0
+    # a power-of-two capacity is required of the probing kinds, not of direct tables
+    plans[2] = plan(1, 1 << 24, 7, crys.HASH_MULT)
+    arr = (crys.crys_plan * 3)(*plans)
+    assert L.crys_run_plans_tagged_bytes(C.byref(t), arr, 3, C.byref(b)) == crys.EINVAL
+    assert L.crys_run_plans_tagged_bytes(C.byref(t), arr, 40, C.byref(b)) == crys.EINVAL
+    assert L.crys_run_plans_tagged_bytes(C.byref(t), arr, 1, None) == crys.EINVAL
+    # misaligned scratch is rejected before anything is enqueued
+    assert L.crys_run_plans_tagged(C.byref(t), arr, 1, 0, 1000, 0, C.c_void_p(8), 64, None) == crys.EINVAL
+    assert L.crys_run_plans_tagged(C.byref(t), arr, 1, 2, 1000, 0, None, 0, None) == crys.EINVAL

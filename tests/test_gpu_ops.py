@@ -134,6 +134,35 @@ def test_probe_identity_hash(crys, orc, dense):
     assert (int(s.item()), int(m.item())) == orc.join_sum(bk, bv, fk, pay)
 
 
+@pytest.mark.parametrize("nb", [1, 5000, 100_003])
+def test_probe_direct_table(crys, orc, nb):
+    # direct table: slot k holds key k (capacity = nb, no power of two); probe keys
+    # outside [0, nb), negative ones included, are absent without a lookup
+    bk = datagen.perm_i32(6, 1, nb)
+    bv = datagen.uniform_i32(6, 2, nb, -100, 100)
+    fk = datagen.uniform_i32(6, 3, 700_001, -50, nb + 50)
+    pay = datagen.uniform_i32(6, 4, 700_001, 1, 100)
+    ht = crys.HashTable.build(_dev(bk), _dev(bv), kind=crys.HASH_DIRECT)
+    assert ht.capacity == nb
+    s, m = crys.probe_aggregate(_dev(fk), _dev(pay), ht)
+    assert (int(s.item()), int(m.item())) == orc.join_sum(bk, bv, fk, pay)
+    slots = ht.slots.cpu().numpy().view(np.uint64)
+    assert np.array_equal((slots & np.uint64(0xFFFFFFFF)).astype(np.int64), np.arange(nb))
+
+
+def test_direct_table_rejects_keys_outside(crys):
+    keys = np.array([0, 1, 2, 7], np.int32)              # 7 >= capacity 4
+    ht = crys.HashTable(4, "cuda", kind=crys.HASH_DIRECT)
+    crys.crys_hash_init(ht.struct)
+    crys.crys_hash_build(_dev(keys), None, 4, [], ht.struct)
+    assert crys.crys_device_errors(clear=True) & crys.DEV_BAD_KEY
+    dup = np.array([0, 1, 1], np.int32)
+    ht = crys.HashTable(4, "cuda", kind=crys.HASH_DIRECT)
+    crys.crys_hash_init(ht.struct)
+    crys.crys_hash_build(_dev(dup), None, 3, [], ht.struct)
+    assert crys.crys_device_errors(clear=True) & crys.DEV_DUP_KEY
+
+
 def test_hash_table_contents(crys):
     n = 50_000
     keys = datagen.perm_i32(3, 4, n) * 7 - 100_000       # sparse, negative keys
