@@ -653,27 +653,21 @@ __global__ void __launch_bounds__(THREADS, (24 * kWarp) / THREADS > 0 ? (24 * kW
 
 constexpr int kMaxTagPairs = 8;
 constexpr int kMaxTagEntries = CRYS_MAX_PLANS * CRYS_MAX_JOINS;
-// Words of a query's descriptor in shared memory; odd, so that lanes reading the same
-// field of different queries fall in different banks.
-constexpr int kDescWords = 61;
+// A query's descriptor in shared memory: 16-byte groups of fields read with vector
+// loads.  Lanes finishing pairs of different queries read the same group of different
+// descriptors; a stride of 17 groups puts 8 such lanes in 8 different bank quadruples.
+// Unused predicates and groups hold entries that always pass, so every lane runs the
+// same instructions whatever query it finishes.
+constexpr int kDescWords = 68;
 enum DescField : int {
-  kDPreds = 0,        // number of fact predicates
-  kDPredCol = 1,      // 8 columns
-  kDPredLo = 9,       // 8 lower bounds
-  kDPredSpan = 17,    // 8 spans (hi - lo)
-  kDGroups = 25,      // grouped joins
-  kDGPair = 26,       // 4 pair indexes
-  kDGShift = 30,      // 4
-  kDGMask = 34,       // 4
-  kDGCard = 38,       // 4
-  kDGStride = 42,     // 4
-  kDAggOp = 46,
-  kDAggA = 47,
-  kDAggB = 48,
-  kDAccMode = 49,
-  kDAccOff = 50,
-  kDSums = 51,        // 2 words
-  kDCounts = 53,      // 2 words
+  kDAggA = 0, kDAggB = 1, kDAccMode = 2, kDAccOff = 3,       // group 0
+  kDP0Col = 4, kDP0Lo = 5, kDP0Span = 6, kDP1Col = 7,        // group 1: fact predicates 0, 1
+  kDP1Lo = 8, kDP1Span = 9, kDPreds = 10, kDGroups = 11,     // group 2
+  kDMulAB = 12, kDCoefA = 13, kDCoefB = 14,                  // group 3: val = a*b or ca*a + cb*b
+  kDGroup0 = 16,      // 4 groups of 4 words: pair << 8 | shift, mask, card, stride
+  kDSums = 32,        // 2 words, then counts (2 words)
+  kDCounts = 34,
+  kDMorePreds = 36,   // predicates 2..7: column, lo, span
 };
 
 struct TagPair {
@@ -741,53 +735,57 @@ struct TagArgs {
   int32_t desc[CRYS_MAX_PLANS * kDescWords];
 };
 
+__device__ __forceinline__ int4 lds4(const int32_t* p) { return *reinterpret_cast<const int4*>(p); }
+
 // Finishes one (row, query) pair whose dimension verdicts all passed: fact predicates,
 // group code from the pairs' values, aggregate, accumulation.
 template <int TILE>
 __device__ __forceinline__ void finish_pair(const int32_t* D, const int32_t* const* cols, int64_t grow, int r,
                                             const int32_t* pv, const SharedAcc& acc, int32_t* err) {
-  const int32_t agg_op = D[kDAggOp];
-  const int32_t xa = ld_cached(cols[D[kDAggA]] + grow);
-  const int32_t xb = agg_op != CRYS_AGG_A ? ld_cached(cols[D[kDAggB]] + grow) : 0;
-  const int np = D[kDPreds];
-  if (np > 0) {
-    const int32_t x0 = ld_cached(cols[D[kDPredCol]] + grow);
-    const int32_t x1 = np > 1 ? ld_cached(cols[D[kDPredCol + 1]] + grow) : D[kDPredLo + 1];
-    if (!in_span(x0, D[kDPredLo], static_cast<uint32_t>(D[kDPredSpan]))) return;
-    if (!in_span(x1, D[kDPredLo + 1], static_cast<uint32_t>(D[kDPredSpan + 1]))) return;
-    for (int f = 2; f < np; ++f)
-      if (!in_span(ld_cached(cols[D[kDPredCol + f]] + grow), D[kDPredLo + f],
-                   static_cast<uint32_t>(D[kDPredSpan + f])))
-        return;
+  const int4 g0 = lds4(D), g1 = lds4(D + 4), g2 = lds4(D + 8), g3 = lds4(D + 12);
+  // every column load in flight together: aggregate operands and two predicates
+  const int32_t xa = ld_cached(cols[g0.x] + grow);
+  const int32_t xb = ld_cached(cols[g0.y] + grow);
+  const int32_t x0 = ld_cached(cols[g1.x] + grow);
+  const int32_t x1 = ld_cached(cols[g1.w] + grow);
+  bool ok = in_span(x0, g1.y, static_cast<uint32_t>(g1.z)) & in_span(x1, g2.x, static_cast<uint32_t>(g2.y));
+  for (int f = 2; f < g2.z; ++f) {
+    const int32_t* P = D + kDMorePreds + 3 * (f - 2);
+    ok = ok && in_span(ld_cached(cols[P[0]] + grow), P[1], static_cast<uint32_t>(P[2]));
   }
+  if (!ok) return;
   int32_t gid = 0;
-  const int ng = D[kDGroups];
-  for (int g = 0; g < ng; ++g) {
-    const int32_t v = pv[D[kDGPair + g] * TILE + r];
-    const uint32_t code = (static_cast<uint32_t>(v) >> D[kDGShift + g]) & static_cast<uint32_t>(D[kDGMask + g]);
-    if (code >= static_cast<uint32_t>(D[kDGCard + g])) {
-      set_error(err, CRYS_DEV_BAD_GROUP);
-      return;
-    }
-    gid += static_cast<int32_t>(code) * D[kDGStride + g];
+  uint32_t bad = 0;
+#pragma unroll
+  for (int g = 0; g < 2; ++g) {
+    const int4 G = lds4(D + kDGroup0 + 4 * g);
+    const uint32_t code = (static_cast<uint32_t>(pv[(G.x >> 8) * TILE + r]) >> (G.x & 31)) & static_cast<uint32_t>(G.y);
+    bad |= static_cast<uint32_t>(code >= static_cast<uint32_t>(G.z));
+    gid += static_cast<int32_t>(code) * G.w;
   }
-  const int64_t x = xa, y = xb;
-  int64_t val;
-  switch (agg_op) {
-    case CRYS_AGG_A_MUL_B: val = x * y; break;
-    case CRYS_AGG_A_SUB_B: val = x - y; break;
-    case CRYS_AGG_A_ADD_B: val = x + y; break;
-    default: val = x; break;
+  for (int g = 2; g < g2.w; ++g) {
+    const int4 G = lds4(D + kDGroup0 + 4 * g);
+    const uint32_t code = (static_cast<uint32_t>(pv[(G.x >> 8) * TILE + r]) >> (G.x & 31)) & static_cast<uint32_t>(G.y);
+    bad |= static_cast<uint32_t>(code >= static_cast<uint32_t>(G.z));
+    gid += static_cast<int32_t>(code) * G.w;
   }
-  if (D[kDAccMode] != kAccGlobal) {
-    const int slot = D[kDAccOff] + gid;
+  if (bad) {
+    set_error(err, CRYS_DEV_BAD_GROUP);
+    return;
+  }
+  const int64_t prod = static_cast<int64_t>(xa) * xb;
+  const int64_t lin = static_cast<int64_t>(xa) * g3.y + static_cast<int64_t>(xb) * g3.z;
+  const int64_t val = g3.x ? prod : lin;
+  if (g0.z != kAccGlobal) {
+    const int slot = g0.w + gid;
     atomicAdd(acc.sums + slot, static_cast<unsigned long long>(val));
     atomicAdd(acc.counts + slot, 1u);
   } else {
+    const int4 ptrs = lds4(D + kDSums);
     unsigned long long* sums = reinterpret_cast<unsigned long long*>(
-        (static_cast<uint64_t>(static_cast<uint32_t>(D[kDSums + 1])) << 32) | static_cast<uint32_t>(D[kDSums]));
+        (static_cast<uint64_t>(static_cast<uint32_t>(ptrs.y)) << 32) | static_cast<uint32_t>(ptrs.x));
     unsigned long long* counts = reinterpret_cast<unsigned long long*>(
-        (static_cast<uint64_t>(static_cast<uint32_t>(D[kDCounts + 1])) << 32) | static_cast<uint32_t>(D[kDCounts]));
+        (static_cast<uint64_t>(static_cast<uint32_t>(ptrs.w)) << 32) | static_cast<uint32_t>(ptrs.z));
     atomicAdd(sums + gid, static_cast<unsigned long long>(val));
     if (counts) atomicAdd(counts + gid, 1ull);
   }
@@ -904,7 +902,7 @@ __global__ void __launch_bounds__(THREADS, (24 * kWarp) / THREADS > 0 ? (24 * kW
     unsigned long long* counts = reinterpret_cast<unsigned long long*>(
         (static_cast<uint64_t>(static_cast<uint32_t>(D[kDCounts + 1])) << 32) | static_cast<uint32_t>(D[kDCounts]));
     int64_t groups = 1;
-    for (int g = 0; g < D[kDGroups]; ++g) groups *= D[kDGCard + g];
+    for (int g = 0; g < D[kDGroups]; ++g) groups *= D[kDGroup0 + 4 * g + 2];
     flush_shared<THREADS>(acc, D[kDAccOff], groups, sums, counts);
   }
 }
@@ -1251,27 +1249,47 @@ bool tag_batch(const crys_plan* plans, const DevQuery* q, int n, TagBatch* tb) {
     const DevQuery& Q = q[qi];
     int32_t* D = S.desc + qi * kDescWords;
     if (!Q.never) S.all_mask |= 1u << qi;
+    // fact predicates: the first two in fixed fields (an unused one always passes: any
+    // value of the aggregate column lies in [0, 0 + 2^32 - 1]), the rest in a list
     D[kDPreds] = Q.n_preds;
-    for (int f = 0; f < Q.n_preds; ++f) {
-      D[kDPredCol + f] = Q.pred_col[f];
-      D[kDPredLo + f] = Q.pred_lo[f];
-      D[kDPredSpan + f] = static_cast<int32_t>(Q.pred_span[f]);
+    const int32_t pc[2] = {Q.n_preds > 0 ? Q.pred_col[0] : Q.agg_a, Q.n_preds > 1 ? Q.pred_col[1] : Q.agg_a};
+    const int32_t pl[2] = {Q.n_preds > 0 ? Q.pred_lo[0] : 0, Q.n_preds > 1 ? Q.pred_lo[1] : 0};
+    const uint32_t ps[2] = {Q.n_preds > 0 ? Q.pred_span[0] : 0xFFFFFFFFu, Q.n_preds > 1 ? Q.pred_span[1] : 0xFFFFFFFFu};
+    D[kDP0Col] = pc[0];
+    D[kDP0Lo] = pl[0];
+    D[kDP0Span] = static_cast<int32_t>(ps[0]);
+    D[kDP1Col] = pc[1];
+    D[kDP1Lo] = pl[1];
+    D[kDP1Span] = static_cast<int32_t>(ps[1]);
+    for (int f = 2; f < Q.n_preds; ++f) {
+      D[kDMorePreds + 3 * (f - 2)] = Q.pred_col[f];
+      D[kDMorePreds + 3 * (f - 2) + 1] = Q.pred_lo[f];
+      D[kDMorePreds + 3 * (f - 2) + 2] = static_cast<int32_t>(Q.pred_span[f]);
     }
+    // grouped joins; unused entries give code 0 of cardinality 1
     int ng = 0;
+    for (int g = 0; g < 4; ++g) {
+      D[kDGroup0 + 4 * g] = 0;
+      D[kDGroup0 + 4 * g + 1] = 0;
+      D[kDGroup0 + 4 * g + 2] = 1;
+      D[kDGroup0 + 4 * g + 3] = 0;
+    }
     for (int j = 0; j < Q.n_joins; ++j) {
       const DevJoin& J = Q.joins[j];
       if (J.card <= 0) continue;
-      D[kDGPair + ng] = pair_of[qi][j];
-      D[kDGShift + ng] = static_cast<int32_t>(J.gshift);
-      D[kDGMask + ng] = static_cast<int32_t>(J.gmask);
-      D[kDGCard + ng] = J.card;
-      D[kDGStride + ng] = J.stride;
+      D[kDGroup0 + 4 * ng] = (pair_of[qi][j] << 8) | static_cast<int32_t>(J.gshift);
+      D[kDGroup0 + 4 * ng + 1] = static_cast<int32_t>(J.gmask);
+      D[kDGroup0 + 4 * ng + 2] = J.card;
+      D[kDGroup0 + 4 * ng + 3] = J.stride;
       ++ng;
     }
     D[kDGroups] = ng;
-    D[kDAggOp] = Q.agg_op;
+    // aggregate: a*b, or ca*a + cb*b (a: ca 1 cb 0 with b = a; a-b: 1, -1; a+b: 1, 1)
     D[kDAggA] = Q.agg_a;
-    D[kDAggB] = Q.agg_b;
+    D[kDAggB] = Q.agg_op == CRYS_AGG_A ? Q.agg_a : Q.agg_b;
+    D[kDMulAB] = Q.agg_op == CRYS_AGG_A_MUL_B ? 1 : 0;
+    D[kDCoefA] = Q.agg_op == CRYS_AGG_A_MUL_B ? 0 : 1;
+    D[kDCoefB] = Q.agg_op == CRYS_AGG_A_SUB_B ? -1 : (Q.agg_op == CRYS_AGG_A_ADD_B ? 1 : 0);
     const uint64_t sp = reinterpret_cast<uint64_t>(Q.sums), cp = reinterpret_cast<uint64_t>(Q.counts);
     D[kDSums] = static_cast<int32_t>(static_cast<uint32_t>(sp));
     D[kDSums + 1] = static_cast<int32_t>(static_cast<uint32_t>(sp >> 32));
