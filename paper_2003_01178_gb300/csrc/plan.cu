@@ -83,15 +83,18 @@ struct GlobalCols {
 };
 
 // Column loads that stay in L1: the columns a shared scan's queries read for predicates
-// and aggregates are read by several queries of the batch in a row.
+// and aggregates are read by several queries of the batch in a row.  In L2 they are the
+// first lines to go: the tile is not read again once its queries are done with it.
 __device__ __forceinline__ int4 ld_cached_v4(const int32_t* p) {
   int4 v;
-  asm volatile("ld.global.nc.v4.s32 {%0,%1,%2,%3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p));
+  asm volatile("ld.global.nc.L2::cache_hint.v4.s32 {%0,%1,%2,%3}, [%4], %5;"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "l"(p), "l"(policy_evict_first()));
   return v;
 }
 __device__ __forceinline__ int32_t ld_cached(const int32_t* p) {
   int32_t v;
-  asm volatile("ld.global.nc.s32 %0, [%1];" : "=r"(v) : "l"(p));
+  asm volatile("ld.global.nc.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(policy_evict_first()));
   return v;
 }
 
@@ -410,6 +413,7 @@ __device__ __forceinline__ void prefetch_tile(const int32_t* const* cols, uint32
 }
 
 constexpr int kPrefetchTiles = 2;  // tiles of a block prefetched ahead of the one in work
+constexpr int kTagPrefetchTiles = 1;  // the same for the tagged scan, whose tiles stay in work longer
 
 template <int THREADS, int ITEMS>
 __global__ void __launch_bounds__(THREADS) plan_kernel(const __grid_constant__ PlanArgs a) {
@@ -832,12 +836,12 @@ __global__ void __launch_bounds__(THREADS, (24 * kWarp) / THREADS > 0 ? (24 * kW
   const uint64_t pol = policy_evict_first();
   const uint64_t pol_table = policy_evict_last();
   if (tid == 0)
-    for (int d = 0; d < kPrefetchTiles; ++d) {
+    for (int d = 0; d < kTagPrefetchTiles; ++d) {
       const int64_t tt = blockIdx.x + static_cast<int64_t>(d) * gridDim.x;
       if (tt < ntiles) prefetch_tile(a.cols, a.col_mask, a.row_begin, tt, TILE, nrows);
     }
   for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const int64_t ahead = t + static_cast<int64_t>(kPrefetchTiles) * gridDim.x;
+    const int64_t ahead = t + static_cast<int64_t>(kTagPrefetchTiles) * gridDim.x;
     if (tid == 0 && ahead < ntiles) prefetch_tile(a.cols, a.col_mask, a.row_begin, ahead, TILE, nrows);
     const int64_t row0 = a.row_begin + t * TILE;
     const int valid = static_cast<int>((nrows - t * TILE) < TILE ? (nrows - t * TILE) : TILE);
