@@ -286,6 +286,35 @@ int crys_run_plans_tagged(const crys_table* fact, const crys_plan* plans, int32_
                           int64_t row_begin, int64_t row_end, int flags, void* scratch,
                           int64_t scratch_bytes, crys_stream s);
 
+/* The tagged scan as a fixed, graph-replayable launch for serving loops (no counterpart in
+ * the paper, which runs one query per kernel).  Everything a launch needs - the batch's
+ * query descriptors, pairs, row range, annotation flag and the outputs to clear - lives in
+ * one argument block in device memory:
+ *   crys_tagged_block_bytes  size of the block (host and device copies).
+ *   crys_tagged_prepare      fills a HOST block (plain or pinned memory, not read by the
+ *                            device) for `plans` over rows [row_begin, row_end): outputs are
+ *                            always added to; the n_zero plans listed in zero_plans (indexes
+ *                            into plans) have their sums and counts cleared first; with
+ *                            CRYS_TAG_ANNOTATE the batch's query bitmaps are rebuilt in
+ *                            scratch (needed whenever the batch differs from the one of the
+ *                            previous launch on the same scratch).  CRYS_EINVAL when the batch
+ *                            cannot be tagged or scratch is smaller than
+ *                            crys_run_plans_tagged_bytes(); the caller then uses
+ *                            crys_run_plans_tagged.
+ *   crys_tagged_launch       launches the work of a DEVICE copy of a block: a prepare kernel
+ *                            (clearing, annotation) and the scan.  Its grid and shared memory
+ *                            depend only on the tile shape, so a stream capture of
+ *                            {copy of the block from pinned memory, crys_tagged_launch} can be
+ *                            replayed for every launch of a serving loop.  The tile shape must
+ *                            be the one the block was prepared with; a block prepared for
+ *                            another shape does no work and raises CRYS_DEV_BOUNDS. */
+#define CRYS_TAG_ANNOTATE 0x2
+int crys_tagged_block_bytes(int64_t* bytes);
+int crys_tagged_prepare(const crys_table* fact, const crys_plan* plans, int32_t n_plans,
+                        int64_t row_begin, int64_t row_end, int flags, const int32_t* zero_plans,
+                        int32_t n_zero, void* scratch, int64_t scratch_bytes, void* host_block);
+int crys_tagged_launch(const void* dev_block, crys_stream s);
+
 /* ------------------------------------------------------------------ tile shapes
  * Each operator is compiled for several tile shapes (threads per block x items per
  * thread, Section 3.3).  crys_tile_variants lists them; crys_set_tile picks the one

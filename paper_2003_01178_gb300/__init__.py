@@ -27,6 +27,7 @@ AGG_A, AGG_A_MUL_B, AGG_A_SUB_B, AGG_A_ADD_B = 0, 1, 2, 3
 AGG_OPS = {"sum": AGG_A, "mul": AGG_A_MUL_B, "sub": AGG_A_SUB_B, "add": AGG_A_ADD_B}
 MAX_COLS, MAX_PREDS, MAX_JOINS, MAX_PLANS, MAX_FIELD_PREDS = 16, 8, 4, 32, 2
 ACCUMULATE = 1
+TAG_ANNOTATE = 2
 HASH_MULT, HASH_IDENT, HASH_DIRECT = 0, 1, 2
 OP_SELECT, OP_PROJECT, OP_PROBE, OP_PLAN, OP_SHARED_SCAN, OP_SORT = range(6)
 OP_NAMES = ["select", "project", "probe", "plan", "shared_scan", "sort"]
@@ -106,6 +107,10 @@ def lib():
                                                   C.POINTER(C.c_int64)]
         L.crys_run_plans_tagged.argtypes = [C.POINTER(crys_table), C.POINTER(crys_plan), i32, i64, i64,
                                             C.c_int, p, i64, p]
+        L.crys_tagged_block_bytes.argtypes = [C.POINTER(C.c_int64)]
+        L.crys_tagged_prepare.argtypes = [C.POINTER(crys_table), C.POINTER(crys_plan), i32, i64, i64, C.c_int,
+                                          C.POINTER(C.c_int32), i32, p, i64, p]
+        L.crys_tagged_launch.argtypes = [p, p]
         L.crys_tile_variants.argtypes = [C.c_int, C.POINTER(C.c_int32), C.POINTER(C.c_int32), i32]
         L.crys_set_tile.argtypes = [C.c_int, i32]
         L.crys_get_tile.argtypes = [C.c_int]
@@ -113,7 +118,8 @@ def lib():
                    "crys_hash_build", "crys_probe_aggregate", "crys_sort", "crys_plan_groups",
                    "crys_pack_fields",
                    "crys_run_plan", "crys_run_plans", "crys_run_plans_tagged_bytes",
-                   "crys_run_plans_tagged", "crys_tile_variants", "crys_set_tile",
+                   "crys_run_plans_tagged", "crys_tagged_block_bytes", "crys_tagged_prepare",
+                   "crys_tagged_launch", "crys_tile_variants", "crys_set_tile",
                    "crys_get_tile"):
             getattr(L, fn).restype = C.c_int
         _lib = L
@@ -250,6 +256,26 @@ def crys_run_plans_tagged(fact: crys_table, plans, row_begin: int, row_end: int,
     _check(lib().crys_run_plans_tagged(C.byref(fact), arr, len(plans), row_begin, row_end, flags,
                                        _ptr(scratch), scratch_bytes, _stream(stream)),
            "crys_run_plans_tagged")
+
+
+def crys_tagged_block_bytes() -> int:
+    out = C.c_int64(0)
+    _check(lib().crys_tagged_block_bytes(C.byref(out)), "crys_tagged_block_bytes")
+    return out.value
+
+
+def crys_tagged_prepare(fact: crys_table, plans, row_begin: int, row_end: int, flags: int, zero_plans,
+                        scratch, scratch_bytes: int, host_block: int) -> int:
+    """Fills the host argument block at address `host_block`; returns the status (no raise:
+    CRYS_EINVAL means the batch cannot use the replayable launch)."""
+    arr = (crys_plan * max(1, len(plans)))(*plans)
+    z = (C.c_int32 * max(1, len(zero_plans)))(*zero_plans)
+    return lib().crys_tagged_prepare(C.byref(fact), arr, len(plans), row_begin, row_end, flags, z,
+                                     len(zero_plans), _ptr(scratch), scratch_bytes, host_block)
+
+
+def crys_tagged_launch(dev_block, stream=None) -> None:
+    _check(lib().crys_tagged_launch(_ptr(dev_block), _stream(stream)), "crys_tagged_launch")
 
 
 def crys_tile_variants(op: int) -> list:

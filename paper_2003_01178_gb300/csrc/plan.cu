@@ -697,8 +697,8 @@ struct AnnotateArgs {
   TagEntry entries[kMaxTagEntries];
 };
 
-__global__ void __launch_bounds__(256) annotate_kernel(const __grid_constant__ AnnotateArgs a) {
-  const TagPair& P = a.pairs[blockIdx.y];
+__device__ __forceinline__ void annotate_pair(const AnnotateArgs& a, int pair) {
+  const TagPair& P = a.pairs[pair];
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
   for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < P.limit; i += stride) {
     const uint64_t s = P.slots[i];
@@ -719,6 +719,10 @@ __global__ void __launch_bounds__(256) annotate_kernel(const __grid_constant__ A
   }
 }
 
+__global__ void __launch_bounds__(256) annotate_kernel(const __grid_constant__ AnnotateArgs a) {
+  annotate_pair(a, blockIdx.y);
+}
+
 struct TagScanPair {
   const uint64_t* ann;
   uint32_t limit;
@@ -734,6 +738,8 @@ struct TagArgs {
   int32_t n_queries;
   uint32_t all_mask;  // queries that can qualify at all
   int32_t shared_groups;
+  int32_t tile_shape;  // THREADS << 16 | ITEMS of the shape the arguments were prepared for
+  int32_t smem_bytes;  // dynamic shared memory the launch provides
   int32_t* err;
   TagScanPair pairs[kMaxTagPairs];
   int32_t desc[CRYS_MAX_PLANS * kDescWords];
@@ -810,8 +816,7 @@ struct TagSmem {
 };
 
 template <int THREADS, int ITEMS>
-__global__ void __launch_bounds__(THREADS, (24 * kWarp) / THREADS > 0 ? (24 * kWarp) / THREADS : 1)
-    tagged_scan_kernel(const __grid_constant__ TagArgs a) {
+__device__ __forceinline__ void tagged_scan_body(const TagArgs& a) {
   using L = TagSmem<THREADS, ITEMS>;
   constexpr int TILE = L::TILE;
   constexpr int VEC = ITEMS / 4;
@@ -822,6 +827,15 @@ __global__ void __launch_bounds__(THREADS, (24 * kWarp) / THREADS > 0 ? (24 * kW
   const int32_t** scols = reinterpret_cast<const int32_t**>(smem_raw + L::cols_off);
   int32_t* pv = reinterpret_cast<int32_t*>(smem_raw + L::pv_off);
   uint16_t* list = reinterpret_cast<uint16_t*>(smem_raw + L::list_off(a.n_pairs)) + warp * L::LIST;
+  // arguments prepared for another tile shape, or accumulators past the shared memory
+  // this launch has: refuse the work (uniformly in every block) instead of overrunning
+  uint32_t dyn_smem;
+  asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn_smem));
+  if (a.tile_shape != ((THREADS << 16) | ITEMS) ||
+      L::acc_off(a.n_pairs) + static_cast<size_t>(a.shared_groups) * 12 > dyn_smem) {
+    if (tid == 0) set_error(a.err, CRYS_DEV_BOUNDS);
+    return;
+  }
   const SharedAcc acc = shared_acc(smem_raw + L::acc_off(a.n_pairs), a.shared_groups);
   for (int w = tid; w < a.n_queries * kDescWords; w += THREADS) desc[w] = a.desc[w];
   if (tid < CRYS_MAX_COLS) scols[tid] = a.cols[tid];
@@ -909,6 +923,51 @@ __global__ void __launch_bounds__(THREADS, (24 * kWarp) / THREADS > 0 ? (24 * kW
     for (int g = 0; g < D[kDGroups]; ++g) groups *= D[kDGroup0 + 4 * g + 2];
     flush_shared<THREADS>(acc, D[kDAccOff], groups, sums, counts);
   }
+}
+
+template <int THREADS, int ITEMS>
+__global__ void __launch_bounds__(THREADS, (24 * kWarp) / THREADS > 0 ? (24 * kWarp) / THREADS : 1)
+    tagged_scan_kernel(const __grid_constant__ TagArgs a) {
+  tagged_scan_body<THREADS, ITEMS>(a);
+}
+
+// ------------------------------------------------------------------ graph-replayable launch
+//
+// A serving loop launches the tagged scan once per row segment with a batch that changes
+// at segment boundaries.  Its arguments then live in a device block (TagLaunch) that the
+// host refills, through a pinned copy, before every launch; the launch itself (shape and
+// shared memory fixed per tile shape) never changes, so one CUDA graph of
+// {copy, prepare_kernel, tagged_scan_kernel_dev} can be captured once and replayed.
+
+struct TagLaunch {
+  TagArgs scan;
+  AnnotateArgs ann;
+  int32_t annotate;  // the batch changed since the previous launch: re-tag its pairs
+  int32_t variant;   // tile shape the block was prepared for
+  int32_t n_zero;    // outputs that start at zero in this launch
+  unsigned long long* zero_ptr[2 * CRYS_MAX_PLANS];
+  int64_t zero_words[2 * CRYS_MAX_PLANS];
+};
+
+// blockIdx.y < kMaxTagPairs: annotation of pair y (when asked for); the last row of
+// blocks zeroes the outputs of the queries that join the batch in this launch.
+__global__ void __launch_bounds__(256) prepare_kernel(const TagLaunch* __restrict__ L) {
+  if (blockIdx.y < kMaxTagPairs) {
+    if (L->annotate && static_cast<int>(blockIdx.y) < L->ann.n_pairs) annotate_pair(L->ann, blockIdx.y);
+    return;
+  }
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  for (int z = 0; z < L->n_zero; ++z) {
+    unsigned long long* p = L->zero_ptr[z];
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < L->zero_words[z]; i += stride)
+      p[i] = 0ull;
+  }
+}
+
+template <int THREADS, int ITEMS>
+__global__ void __launch_bounds__(THREADS, (24 * kWarp) / THREADS > 0 ? (24 * kWarp) / THREADS : 1)
+    tagged_scan_kernel_dev(const TagArgs* __restrict__ a) {
+  tagged_scan_body<THREADS, ITEMS>(*a);
 }
 
 // ------------------------------------------------------------------ packing
@@ -1304,32 +1363,20 @@ bool tag_batch(const crys_plan* plans, const DevQuery* q, int n, TagBatch* tb) {
 }
 
 // Places the annotations in scratch and launches the annotation and the scan.
-template <int THREADS, int ITEMS>
-int launch_tagged(TagBatch& tb, const DevQuery* q, unsigned char* scratch, cudaStream_t s) {
-  using L = TagSmem<THREADS, ITEMS>;
-  constexpr int TILE = L::TILE;
-  AnnotateArgs& A = tb.ann;
-  TagArgs& S = tb.scan;
+// Points each pair's annotations into scratch.
+void place_annotations(TagBatch& tb, unsigned char* scratch) {
   int64_t off = 0;
-  for (int p = 0; p < A.n_pairs; ++p) {
-    A.pairs[p].ann = reinterpret_cast<uint64_t*>(scratch + off);
-    S.pairs[p].ann = A.pairs[p].ann;
-    off += (static_cast<int64_t>(A.pairs[p].limit) * 8 + 15) / 16 * 16;
+  for (int p = 0; p < tb.ann.n_pairs; ++p) {
+    tb.ann.pairs[p].ann = reinterpret_cast<uint64_t*>(scratch + off);
+    tb.scan.pairs[p].ann = tb.ann.pairs[p].ann;
+    off += (static_cast<int64_t>(tb.ann.pairs[p].limit) * 8 + 15) / 16 * 16;
   }
-  if (A.n_pairs > 0) {
-    int64_t gx = (tb.max_slots + 255) / 256;
-    const int64_t cap = static_cast<int64_t>(sm_count()) * 8;
-    if (gx > cap) gx = cap;
-    annotate_kernel<<<dim3(static_cast<unsigned>(gx < 1 ? 1 : gx), static_cast<unsigned>(A.n_pairs)), 256, 0, s>>>(A);
-    note_launch();
-    const int rc = check_launch();
-    if (rc != CRYS_OK) return rc;
-  }
-  // Group accumulators in shared memory for as many queries as fit next to the fixed
-  // parts (smallest group counts first); the rest accumulate with global atomics.
-  const size_t fixed = L::acc_off(S.n_pairs);
-  const size_t share = (220u * 1024u) / kScanBlocksPerSM;
-  const size_t budget = share > fixed ? share - fixed : 0;
+}
+
+// Group accumulators in shared memory for as many queries as fit in `budget` bytes
+// (smallest group counts first: they have the most rows per group, where global atomics
+// would contend most); the rest accumulate with global atomics.  Returns the groups held.
+int64_t assign_accumulators(TagArgs& S, const DevQuery* q, size_t budget) {
   int order[CRYS_MAX_PLANS];
   for (int qi = 0; qi < S.n_queries; ++qi) order[qi] = qi;
   for (int i = 1; i < S.n_queries; ++i)
@@ -1352,13 +1399,80 @@ int launch_tagged(TagBatch& tb, const DevQuery* q, unsigned char* scratch, cudaS
     }
   }
   S.shared_groups = static_cast<int32_t>(used);
-  const size_t smem = fixed + static_cast<size_t>(used) * 12;
+  return used;
+}
+
+constexpr size_t kTagShare = (220u * 1024u) / kScanBlocksPerSM;  // shared memory of one block
+
+template <int THREADS, int ITEMS>
+int launch_tagged(TagBatch& tb, const DevQuery* q, unsigned char* scratch, cudaStream_t s) {
+  using L = TagSmem<THREADS, ITEMS>;
+  constexpr int TILE = L::TILE;
+  AnnotateArgs& A = tb.ann;
+  TagArgs& S = tb.scan;
+  place_annotations(tb, scratch);
+  if (A.n_pairs > 0) {
+    int64_t gx = (tb.max_slots + 255) / 256;
+    const int64_t cap = static_cast<int64_t>(sm_count()) * 8;
+    if (gx > cap) gx = cap;
+    annotate_kernel<<<dim3(static_cast<unsigned>(gx < 1 ? 1 : gx), static_cast<unsigned>(A.n_pairs)), 256, 0, s>>>(A);
+    note_launch();
+    const int rc = check_launch();
+    if (rc != CRYS_OK) return rc;
+  }
+  const size_t fixed = L::acc_off(S.n_pairs);
+  const int64_t used = assign_accumulators(S, q, kTagShare > fixed ? kTagShare - fixed : 0);
+  S.tile_shape = (THREADS << 16) | ITEMS;
+  S.smem_bytes = static_cast<int32_t>(fixed + static_cast<size_t>(used) * 12);
   auto k = tagged_scan_kernel<THREADS, ITEMS>;
-  if (!allow_smem(k, smem)) return CRYS_ECUDA;
+  if (!allow_smem(k, S.smem_bytes)) return CRYS_ECUDA;
   const int64_t ntiles = (S.row_end - S.row_begin + TILE - 1) / TILE;
-  const int grid = persistent_grid(k, THREADS, smem, ntiles);
+  const int grid = persistent_grid(k, THREADS, S.smem_bytes, ntiles);
   if (!counts_fit(S.row_end - S.row_begin, grid)) return CRYS_EINVAL;
-  k<<<grid, THREADS, smem, s>>>(S);
+  k<<<grid, THREADS, S.smem_bytes, s>>>(S);
+  note_launch();
+  return check_launch();
+}
+
+// The fixed launch of a TagLaunch block for tile shape (THREADS, ITEMS): grid and shared
+// memory depend only on the shape, so the launch can be captured once and replayed.
+template <int THREADS, int ITEMS>
+int fixed_scan_grid(int* grid) {
+  auto k = tagged_scan_kernel_dev<THREADS, ITEMS>;
+  if (!allow_smem(k, kTagShare)) return CRYS_ECUDA;
+  *grid = persistent_grid(k, THREADS, kTagShare, int64_t{1} << 40);
+  return *grid > 0 ? CRYS_OK : CRYS_ECUDA;
+}
+
+template <int THREADS, int ITEMS>
+int prepare_block(TagBatch& tb, const DevQuery* q, unsigned char* scratch, TagLaunch* out) {
+  using L = TagSmem<THREADS, ITEMS>;
+  place_annotations(tb, scratch);
+  TagArgs& S = tb.scan;
+  const size_t fixed = L::acc_off(S.n_pairs);
+  if (fixed > kTagShare) return CRYS_EINVAL;
+  assign_accumulators(S, q, kTagShare - fixed);
+  S.tile_shape = (THREADS << 16) | ITEMS;
+  S.smem_bytes = static_cast<int32_t>(kTagShare);
+  int grid = 0;
+  const int rc = fixed_scan_grid<THREADS, ITEMS>(&grid);
+  if (rc != CRYS_OK) return rc;
+  if (!counts_fit(S.row_end - S.row_begin, grid)) return CRYS_EINVAL;
+  out->scan = S;
+  out->ann = tb.ann;
+  return CRYS_OK;
+}
+
+template <int THREADS, int ITEMS>
+int launch_block(const TagLaunch* dev, cudaStream_t s) {
+  int grid = 0;
+  int rc = fixed_scan_grid<THREADS, ITEMS>(&grid);
+  if (rc != CRYS_OK) return rc;
+  prepare_kernel<<<dim3(static_cast<unsigned>(sm_count() * 4), kMaxTagPairs + 1), 256, 0, s>>>(dev);
+  note_launch();
+  rc = check_launch();
+  if (rc != CRYS_OK) return rc;
+  tagged_scan_kernel_dev<THREADS, ITEMS><<<grid, THREADS, kTagShare, s>>>(&dev->scan);
   note_launch();
   return check_launch();
 }
@@ -1577,6 +1691,90 @@ int crys_run_plans_tagged(const crys_table* fact, const crys_plan* plans, int32_
   delete tb;
   delete[] q;
   return rc;
+}
+
+int crys_tagged_block_bytes(int64_t* bytes) {
+  if (!bytes) return CRYS_EINVAL;
+  *bytes = (static_cast<int64_t>(sizeof(crys::TagLaunch)) + 255) / 256 * 256;
+  return CRYS_OK;
+}
+
+int crys_tagged_prepare(const crys_table* fact, const crys_plan* plans, int32_t n_plans, int64_t row_begin,
+                        int64_t row_end, int flags, const int32_t* zero_plans, int32_t n_zero, void* scratch,
+                        int64_t scratch_bytes, void* host_block) {
+  using namespace crys;
+  if (!host_block || check_table(fact) != CRYS_OK || n_plans < 1 || n_plans > CRYS_MAX_PLANS || !plans)
+    return CRYS_EINVAL;
+  if (row_begin < 0 || row_end < row_begin || row_end > fact->n_rows || (row_begin & 3)) return CRYS_EINVAL;
+  if ((flags & ~CRYS_TAG_ANNOTATE) || n_zero < 0 || n_zero > n_plans || (n_zero > 0 && !zero_plans))
+    return CRYS_EINVAL;
+  if (!scratch || !aligned16(scratch) || scratch_bytes < 0) return CRYS_EINVAL;
+  DevQuery* q = new DevQuery[CRYS_MAX_PLANS]();
+  TagBatch* tb = new TagBatch();
+  TagLaunch* out = static_cast<TagLaunch*>(host_block);
+  uint32_t mask = 0;
+  int rc = CRYS_OK;
+  for (int qi = 0; qi < n_plans && rc == CRYS_OK; ++qi) {
+    uint32_t m = 0;
+    rc = to_device(*fact, plans[qi], &q[qi], &m);
+    mask |= m;
+  }
+  if (rc == CRYS_OK && (!tag_batch(plans, q, n_plans, tb) || tb->bytes > scratch_bytes)) rc = CRYS_EINVAL;
+  if (rc == CRYS_OK) {
+    TagArgs& S = tb->scan;
+    for (int c = 0; c < CRYS_MAX_COLS; ++c) S.cols[c] = c < fact->n_cols ? fact->cols[c] : nullptr;
+    S.col_mask = mask;
+    S.row_begin = row_begin;
+    S.row_end = row_end;
+    S.err = device_error_word();
+    if (!S.err) rc = CRYS_ECUDA;
+  }
+  if (rc == CRYS_OK) {
+    unsigned char* base = static_cast<unsigned char*>(scratch);
+    constexpr int kOp = CRYS_OP_SHARED_SCAN;
+    const int v = tile_variant(kOp);
+    switch (v) {
+      case 1: rc = prepare_block<kTiles[kOp][1].threads, kTiles[kOp][1].items>(*tb, q, base, out); break;
+      case 2: rc = prepare_block<kTiles[kOp][2].threads, kTiles[kOp][2].items>(*tb, q, base, out); break;
+      case 3: rc = prepare_block<kTiles[kOp][3].threads, kTiles[kOp][3].items>(*tb, q, base, out); break;
+      default: rc = prepare_block<kTiles[kOp][0].threads, kTiles[kOp][0].items>(*tb, q, base, out); break;
+    }
+    out->variant = v;
+  }
+  if (rc == CRYS_OK) {
+    out->annotate = (flags & CRYS_TAG_ANNOTATE) ? 1 : 0;
+    out->n_zero = 0;
+    for (int z = 0; z < n_zero && rc == CRYS_OK; ++z) {
+      const int qi = zero_plans[z];
+      if (qi < 0 || qi >= n_plans) {
+        rc = CRYS_EINVAL;
+        break;
+      }
+      out->zero_ptr[out->n_zero] = q[qi].sums;
+      out->zero_words[out->n_zero++] = q[qi].groups;
+      if (q[qi].counts) {
+        out->zero_ptr[out->n_zero] = q[qi].counts;
+        out->zero_words[out->n_zero++] = q[qi].groups;
+      }
+    }
+  }
+  delete tb;
+  delete[] q;
+  return rc;
+}
+
+int crys_tagged_launch(const void* dev_block, crys_stream stream) {
+  using namespace crys;
+  if (!dev_block || !aligned16(dev_block)) return CRYS_EINVAL;
+  const TagLaunch* L = static_cast<const TagLaunch*>(dev_block);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  constexpr int kOp = CRYS_OP_SHARED_SCAN;
+  switch (tile_variant(kOp)) {
+    case 1: return launch_block<kTiles[kOp][1].threads, kTiles[kOp][1].items>(L, s);
+    case 2: return launch_block<kTiles[kOp][2].threads, kTiles[kOp][2].items>(L, s);
+    case 3: return launch_block<kTiles[kOp][3].threads, kTiles[kOp][3].items>(L, s);
+    default: return launch_block<kTiles[kOp][0].threads, kTiles[kOp][0].items>(L, s);
+  }
 }
 
 }  // extern "C"

@@ -11,6 +11,11 @@ hash tables plus outputs fit in ``memory_budget`` bytes next to the active queri
 its dimension tables are built (on the same stream) when it is admitted and released
 when it completes.  Results are identical to running the query alone: integer sums,
 every fact row counted exactly once.
+
+With ``graphs=True`` (resident mode) every launch is a replay of a captured CUDA graph
+(``ReplayedScan``): the host only writes the launch's argument block to pinned memory;
+a query's outputs are cleared by its first launch and the batch is re-tagged only when
+it changed.
 """
 from __future__ import annotations
 
@@ -21,7 +26,7 @@ import numpy as np
 import torch
 
 from . import MAX_PLANS, check_device_errors
-from .starschema import CompiledQuery, ResidentStarSchema
+from .starschema import CompiledQuery, ReplayedScan, ResidentStarSchema
 
 
 @dataclass
@@ -48,6 +53,7 @@ class ServeStats:
     launches: int = 0
     deferred: int = 0
     max_active: int = 0
+    replays: int = 0                      # launches that were CUDA graph replays
     latencies_s: list = field(default_factory=list)
 
     @property
@@ -61,7 +67,7 @@ class ServeStats:
 class QueryServer:
     def __init__(self, store: ResidentStarSchema, segments: int = 8, max_slots: int = MAX_PLANS,
                  memory_budget: int = 8 << 30, stream: torch.cuda.Stream | None = None,
-                 mode: str = "resident"):
+                 mode: str = "resident", graphs: bool = True):
         if not 1 <= max_slots <= MAX_PLANS:
             raise ValueError("max_slots must be in 1..32")
         self.store = store
@@ -74,6 +80,7 @@ class QueryServer:
         step = (step + 4095) // 4096 * 4096           # segment starts stay 16-byte aligned
         self.bounds = [(b, min(n, b + step)) for b in range(0, n, step)] or [(0, 0)]
         self.next_segment = 0
+        self.replay = ReplayedScan(store, self.stream) if graphs and mode == "resident" else None
 
     # -- admission ----------------------------------------------------------------------
     def fits(self, req: Request, active: list) -> bool:
@@ -82,17 +89,24 @@ class QueryServer:
 
     def _admit(self, req: Request, now: float) -> None:
         with torch.cuda.stream(self.stream):
-            req.compiled = self.store.compile(req.query, mode=self.mode, stream=self.stream)
+            req.compiled = self.store.compile(req.query, mode=self.mode, stream=self.stream,
+                                              zero=self.replay is None)
         req.admitted_s = now
         req.seen = 0
 
     # -- one launch -------------------------------------------------------------------
     def _launch(self, active: list) -> None:
         b, e = self.bounds[self.next_segment]
-        # outputs start at zero when a query is compiled, so every launch accumulates
-        with torch.cuda.stream(self.stream):
-            self.store.run_shared([r.compiled for r in active], b, e, accumulate=True,
-                                  stream=self.stream)
+        cqs = [r.compiled for r in active]
+        fresh = [i for i, r in enumerate(active) if r.seen == 0]
+        if self.replay is None or not self.replay.launch(cqs, b, e, fresh):
+            with torch.cuda.stream(self.stream):
+                if self.replay is not None:          # outputs were left for the replay to clear
+                    for i in fresh:
+                        cqs[i].sums.zero_()
+                        cqs[i].counts.zero_()
+                # outputs start at zero, so every launch accumulates
+                self.store.run_shared(cqs, b, e, accumulate=True, stream=self.stream)
         for r in active:
             r.seen += 1
         self.next_segment = (self.next_segment + 1) % len(self.bounds)
@@ -121,6 +135,7 @@ class QueryServer:
         stats = ServeStats()
         nseg = len(self.bounds)
         torch.cuda.synchronize(self.store.device)
+        replays0 = self.replay.replays if self.replay is not None else 0
         t0 = time.perf_counter()
         inflight = None   # (event, finishing requests) of the launch on the GPU
         while pi < len(pending) or active or inflight:
@@ -163,6 +178,7 @@ class QueryServer:
                     if wait > 0:
                         time.sleep(min(wait, 0.001))
         stats.wall_s = time.perf_counter() - t0
+        stats.replays = (self.replay.replays - replays0) if self.replay is not None else 0
         check_device_errors(self.stream)
         return reqs, stats
 

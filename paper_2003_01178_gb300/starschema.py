@@ -21,14 +21,16 @@ Both shapes give identical results (integer sums and counts per group).
 """
 from __future__ import annotations
 
+import itertools
 import math
 from dataclasses import dataclass, field
 
 import torch
 
 from . import (HashTable, crys_hash_build, crys_hash_init, crys_pack_fields, crys_run_plan,
-               crys_run_plans_tagged, crys_run_plans_tagged_bytes, make_plan, make_table,
-               capacity_for, ACCUMULATE, MAX_PLANS, HASH_DIRECT, HASH_IDENT)
+               crys_run_plans_tagged, crys_run_plans_tagged_bytes, crys_tagged_block_bytes,
+               crys_tagged_launch, crys_tagged_prepare, make_plan, make_table, capacity_for,
+               ACCUMULATE, MAX_PLANS, HASH_DIRECT, HASH_IDENT, OK, TAG_ANNOTATE)
 
 
 @dataclass
@@ -46,6 +48,7 @@ class CompiledQuery:
     counts: torch.Tensor
     tables: list = field(default_factory=list)   # per-query HashTables kept alive with the plan
     groups: int = 1
+    serial: int = field(default_factory=itertools.count().__next__)   # unique per compiled plan
 
     @property
     def table_bytes(self) -> int:
@@ -96,7 +99,10 @@ class ResidentStarSchema:
                                                    kind=HASH_DIRECT)
             else:
                 self.resident[d] = HashTable.build(keys, packed, stream=stream, kind=HASH_IDENT)
-        self._scratch = None                          # query bitmaps of the latest shared scan
+        # query bitmaps of the latest shared scan: one 8-byte entry per slot of each
+        # (fact column, table) pair; each resident table is joined through one column
+        need = sum((t.capacity * 8 + 15) // 16 * 16 for t in self.resident.values())
+        self._scratch = torch.empty(max(need, 16), dtype=torch.uint8, device=self.device)
 
     @property
     def resident_bytes(self) -> int:
@@ -131,7 +137,9 @@ class ResidentStarSchema:
         return tb + 16 * self.groups(query)
 
     # -- compilation ----------------------------------------------------------------
-    def compile(self, query: dict, mode: str = "resident", stream=None) -> CompiledQuery:
+    def compile(self, query: dict, mode: str = "resident", stream=None, zero: bool = True) -> CompiledQuery:
+        """Plan of one query; with zero=False its outputs are left uninitialised (a
+        replayed scan clears them in the query's first launch)."""
         names = self.schema.fact_cols
         preds = [(names.index(c), lo, hi) for (c, lo, hi) in query["fact_preds"]]
         joins, tables = [], []
@@ -159,8 +167,9 @@ class ResidentStarSchema:
         op, a, b = query["agg"]
         agg = (op, names.index(a), names.index(b) if b is not None else None)
         g = self.groups(query)
-        sums = torch.zeros(g, dtype=torch.int64, device=self.device)
-        counts = torch.zeros(g, dtype=torch.int64, device=self.device)
+        alloc = torch.zeros if zero else torch.empty
+        sums = alloc(g, dtype=torch.int64, device=self.device)
+        counts = alloc(g, dtype=torch.int64, device=self.device)
         plan = make_plan(preds, joins, agg, sums, counts)
         return CompiledQuery(query, plan, sums, counts, tables, g)
 
@@ -168,6 +177,11 @@ class ResidentStarSchema:
     def run(self, cq: CompiledQuery, stream=None) -> None:
         """One query, one fused probe kernel over all fact rows."""
         crys_run_plan(self.table, cq.plan, stream)
+
+    def scratch(self, need: int) -> torch.Tensor:
+        if self._scratch.numel() < need:
+            self._scratch = torch.empty(need, dtype=torch.uint8, device=self.device)
+        return self._scratch
 
     def run_shared(self, cqs: list, row_begin: int = 0, row_end: int | None = None,
                    accumulate: bool = False, stream=None) -> None:
@@ -178,9 +192,7 @@ class ResidentStarSchema:
         row_end = self.n_rows if row_end is None else row_end
         plans = [c.plan for c in cqs]
         need = crys_run_plans_tagged_bytes(self.table, plans)
-        if need and (self._scratch is None or self._scratch.numel() < need):
-            self._scratch = torch.empty(need, dtype=torch.uint8, device=self.device)
-        scratch = self._scratch if need else None
+        scratch = self.scratch(need) if need else None
         crys_run_plans_tagged(self.table, plans, row_begin, row_end, ACCUMULATE if accumulate else 0,
                               scratch, scratch.numel() if need else 0, stream)
 
@@ -202,3 +214,61 @@ def served_schema() -> Schema:
     import datagen
     return Schema(list(datagen.SS_FACT_COLS),
                   {d: {"fk": s["fk"], "attrs": dict(s["attrs"])} for d, s in datagen.SS_DIMS.items()})
+
+
+class ReplayedScan:
+    """Tagged shared scans of a serving loop through captured CUDA graphs.
+
+    A launch's arguments go to a pinned host block (``crys_tagged_prepare``); the graph
+    replays {copy of the block to the device, ``crys_tagged_launch``}.  Two pinned blocks
+    alternate, each with its own graph, so the host prepares launch k+1 while launch k
+    runs; a block is rewritten only after the replay that read it has finished."""
+
+    def __init__(self, store: ResidentStarSchema, stream: torch.cuda.Stream):
+        self.store = store
+        self.stream = stream
+        nb = crys_tagged_block_bytes()
+        self.dev_block = torch.empty(nb, dtype=torch.uint8, device=store.device)
+        self.host = [torch.empty(nb, dtype=torch.uint8, pin_memory=True) for _ in range(2)]
+        self.graphs = [None, None]
+        self.done = [None, None]
+        self.k = 0
+        self.replays = 0
+        self._batch = None
+
+    def _capture(self, i: int) -> None:
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self.dev_block.copy_(self.host[i], non_blocking=True)
+            crys_tagged_launch(self.dev_block)
+        self.graphs[i] = g
+
+    def launch(self, cqs: list, row_begin: int, row_end: int, zero: list) -> bool:
+        """One launch of `cqs` over rows [row_begin, row_end), adding to their outputs
+        after clearing those of the plans listed in `zero`; False when the batch cannot
+        use the replayed launch (nothing was enqueued)."""
+        plans = [c.plan for c in cqs]
+        need = crys_run_plans_tagged_bytes(self.store.table, plans)
+        if not need:
+            return False
+        scratch = self.store.scratch(need)
+        batch = (tuple(c.serial for c in cqs), scratch.data_ptr())
+        i = self.k % 2
+        if self.done[i] is not None:
+            self.done[i].synchronize()
+        flags = TAG_ANNOTATE if batch != self._batch else 0
+        rc = crys_tagged_prepare(self.store.table, plans, row_begin, row_end, flags, list(zero), scratch,
+                                 scratch.numel(), self.host[i].data_ptr())
+        if rc != OK:
+            return False
+        if self.graphs[i] is None:
+            self._capture(i)
+        with torch.cuda.stream(self.stream):
+            self.graphs[i].replay()
+            ev = torch.cuda.Event()
+            ev.record(self.stream)
+        self.done[i] = ev
+        self._batch = batch
+        self.k += 1
+        self.replays += 1
+        return True

@@ -134,3 +134,31 @@ def test_tagged_scan_scratch_sizing(crys):
     # misaligned scratch is rejected before anything is enqueued
     assert L.crys_run_plans_tagged(C.byref(t), arr, 1, 0, 1000, 0, C.c_void_p(8), 64, None) == crys.EINVAL
     assert L.crys_run_plans_tagged(C.byref(t), arr, 1, 2, 1000, 0, None, 0, None) == crys.EINVAL
+
+
+def test_replayable_launch_host_checks(crys):
+    """Argument-block entry points: size query, and rejection of bad arguments before
+    any device work (no GPU needed)."""
+    L = crys.lib()
+    b = C.c_int64(0)
+    assert L.crys_tagged_block_bytes(C.byref(b)) == crys.OK and b.value > 0 and b.value % 256 == 0
+    assert L.crys_tagged_block_bytes(None) == crys.EINVAL
+    t = crys.crys_table()
+    t.n_cols = 1
+    t.n_rows = 100
+    t.cols[0] = 4096
+    p = crys.crys_plan()
+    p.d_sums = 1 << 20
+    arr = (crys.crys_plan * 1)(p)
+    hb = (C.c_uint8 * b.value)()
+    z = (C.c_int32 * 1)(0)
+    args = dict(fact=C.byref(t), plans=arr)
+    # no block, no plans, bad flags, bad zero list, misaligned scratch, odd row start
+    assert L.crys_tagged_prepare(C.byref(t), arr, 1, 0, 100, 0, z, 0, C.c_void_p(4096), 64, None) == crys.EINVAL
+    assert L.crys_tagged_prepare(C.byref(t), arr, 0, 0, 100, 0, z, 0, C.c_void_p(4096), 64, hb) == crys.EINVAL
+    assert L.crys_tagged_prepare(C.byref(t), arr, 1, 0, 100, 0x10, z, 0, C.c_void_p(4096), 64, hb) == crys.EINVAL
+    assert L.crys_tagged_prepare(C.byref(t), arr, 1, 0, 100, 0, None, 1, C.c_void_p(4096), 64, hb) == crys.EINVAL
+    assert L.crys_tagged_prepare(C.byref(t), arr, 1, 0, 100, 0, z, 0, C.c_void_p(4100), 64, hb) == crys.EINVAL
+    assert L.crys_tagged_prepare(C.byref(t), arr, 1, 2, 100, 0, z, 0, C.c_void_p(4096), 64, hb) == crys.EINVAL
+    assert L.crys_tagged_launch(None, None) == crys.EINVAL
+    del args
