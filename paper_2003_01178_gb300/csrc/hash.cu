@@ -4,7 +4,8 @@
 // Probe kernel per tile: BlockLoad of the key and payload tiles (bulk copies into a
 // shared-memory stage), BlockLookup with the first slot of every item loaded before any
 // is resolved (ITEMS independent random reads in flight per thread), per-thread int64
-// sums, and BlockAggregate once per persistent block (one atomic per block).
+// sums, and BlockAggregate once per persistent block (one atomic per block).  A table of
+// at most 32 KB is first copied into each block's shared memory and probed there.
 #include "common.cuh"
 #include "pipeline.cuh"
 #include "tiles.h"
@@ -80,9 +81,14 @@ struct ProbeArgs {
   unsigned long long* matches;
   int32_t* err;
   int32_t stages;
+  int32_t table_slots;  // SMEM_TABLE: the whole table, copied into shared memory
 };
 
-template <int THREADS, int ITEMS>
+// A table of at most this many bytes is copied into every block's shared memory: random
+// slot reads then cost shared-memory wavefronts instead of L1 tag lookups.
+constexpr int64_t kSmemTableBytes = 32 * 1024;
+
+template <int THREADS, int ITEMS, bool SMEM_TABLE>
 __global__ void __launch_bounds__(THREADS) probe_kernel(ProbeArgs a) {
   constexpr int TILE = THREADS * ITEMS;
   constexpr int VEC = ITEMS / 4;
@@ -116,7 +122,23 @@ __global__ void __launch_bounds__(THREADS) probe_kernel(ProbeArgs a) {
   ring_init(ring, S);
   if (tid == 0)
     for (int s = 0; s < S; ++s) issue(s);
+  uint64_t* tbl = reinterpret_cast<uint64_t*>(stages + S * 2 * TILE);
+  if (SMEM_TABLE)
+    for (int i = tid; i < a.table_slots; i += THREADS) tbl[i] = ld_slot(a.slots + i, pol_table);
   __syncthreads();
+  // Linear probing continued in the shared-memory copy of the table.
+  auto resolve_smem = [&](uint32_t h, uint64_t sl, int32_t key, int32_t* value) -> bool {
+    for (uint32_t probe = 0;; ++probe) {
+      if (sl == kEmptySlot) return false;
+      if (static_cast<uint32_t>(sl) == static_cast<uint32_t>(key)) {
+        *value = static_cast<int32_t>(sl >> 32);
+        return true;
+      }
+      if (probe >= a.hash.steps) return false;
+      h = (h + 1) & a.hash.mask;
+      sl = tbl[h];
+    }
+  };
 
   bool aborted = false;
   for (int64_t k = 0;; ++k) {
@@ -151,13 +173,18 @@ __global__ void __launch_bounds__(THREADS) probe_kernel(ProbeArgs a) {
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
       h[i] = hash_slot(key[i], a.hash);
-      slot[i] = ((live >> i) & 1u) && hash_may_hold(key[i], a.hash) ? ld_slot(a.slots + h[i], pol_table)
-                                                                      : kEmptySlot;
+      const bool look = ((live >> i) & 1u) && hash_may_hold(key[i], a.hash);
+      if (SMEM_TABLE)
+        slot[i] = look ? tbl[h[i]] : kEmptySlot;
+      else
+        slot[i] = look ? ld_slot(a.slots + h[i], pol_table) : kEmptySlot;
     }
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
       int32_t value;
-      if (((live >> i) & 1u) && hash_resolve(a.slots, a.hash, h[i], slot[i], key[i], &value, pol_table)) {
+      const bool hit = SMEM_TABLE ? resolve_smem(h[i], slot[i], key[i], &value)
+                                  : hash_resolve(a.slots, a.hash, h[i], slot[i], key[i], &value, pol_table);
+      if (((live >> i) & 1u) && hit) {
         sum += static_cast<uint64_t>(static_cast<int64_t>(pay[i]) * static_cast<int64_t>(value));
         matches += 1;
       }
@@ -184,11 +211,18 @@ int launch_probe(ProbeArgs a, cudaStream_t s) {
   // Probes need warps more than deep staging, and a small table wants L1 left over:
   // two stages per block.
   a.stages = 2;
-  const size_t smem = static_cast<size_t>(a.stages) * 2 * TILE * sizeof(int32_t);
+  const size_t stage_bytes = static_cast<size_t>(a.stages) * 2 * TILE * sizeof(int32_t);
   const int64_t ntiles = (a.n + TILE - 1) / TILE;
-  auto k = probe_kernel<THREADS, ITEMS>;
-  if (!allow_smem(k, smem)) return CRYS_ECUDA;
-  k<<<persistent_grid(k, THREADS, smem, ntiles), THREADS, smem, s>>>(a);
+  if (a.table_slots > 0) {
+    const size_t smem = stage_bytes + static_cast<size_t>(a.table_slots) * 8;
+    auto k = probe_kernel<THREADS, ITEMS, true>;
+    if (!allow_smem(k, smem)) return CRYS_ECUDA;
+    k<<<persistent_grid(k, THREADS, smem, ntiles), THREADS, smem, s>>>(a);
+  } else {
+    auto k = probe_kernel<THREADS, ITEMS, false>;
+    if (!allow_smem(k, stage_bytes)) return CRYS_ECUDA;
+    k<<<persistent_grid(k, THREADS, stage_bytes, ntiles), THREADS, stage_bytes, s>>>(a);
+  }
   note_launch();
   return check_launch();
 }
@@ -269,6 +303,7 @@ int crys_probe_aggregate(const int32_t* fk, const int32_t* payload, int64_t n, c
   a.matches = reinterpret_cast<unsigned long long*>(d_matches);
   a.err = device_error_word();
   if (!a.err) return CRYS_ECUDA;
+  a.table_slots = ht->capacity * 8 <= kSmemTableBytes ? static_cast<int32_t>(ht->capacity) : 0;
   switch (tile_variant(kOp)) {
     case 1: return launch_probe<kTiles[kOp][1].threads, kTiles[kOp][1].items>(a, s);
     case 2: return launch_probe<kTiles[kOp][2].threads, kTiles[kOp][2].items>(a, s);
