@@ -166,6 +166,34 @@ def l2_flush(buf):
     buf.zero_()
 
 
+def graph_differential_ms(fn, flush, k=20, rounds=7):
+    """Device time of one launch of `fn` after an L2 flush, free of per-launch host and
+    event overhead: two CUDA graphs, k x {flush, fn} and k x {flush}, each replayed
+    `rounds` times and timed with events; (median1 - median0) / k."""
+    import torch
+    g1, g0 = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
+    fn()                                   # first call outside capture (attributes, caches)
+    with torch.cuda.graph(g1):
+        for _ in range(k):
+            flush()
+            fn()
+    with torch.cuda.graph(g0):
+        for _ in range(k):
+            flush()
+    stream = torch.cuda.current_stream()
+    t1, t0 = [], []
+    for _ in range(rounds):
+        for g, out in ((g1, t1), (g0, t0)):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            g.replay()
+            b.record(stream)
+            b.synchronize()
+            out.append(a.elapsed_time(b))
+    return max(0.0, (statistics.median(t1) - statistics.median(t0)) / k)
+
+
 # ----------------------------------------------------------------------------- served
 
 def served_store(seed, n_rows, dim_scale, device):
@@ -195,7 +223,8 @@ def run_served(args, rank, world, local):
 
     def one_step(step, timers=None):
         qs = batch_queries(seed, step, rank)
-        cqs = [store.compile(q, mode="resident") for q in qs]
+        # outputs are cleared by the shared scan itself (it does not accumulate here)
+        cqs = [store.compile(q, mode="resident", zero=False) for q in qs]
         if timers is not None:
             with timers:
                 store.run_shared(cqs)
@@ -466,8 +495,12 @@ def run_operator(args, rank, world, local):
             x = dgd.uniform_i32(seed, datagen.STREAMS["sel.x"], n, 0, (1 << 31) - 1, dev)
             out = torch.empty(n, dtype=torch.int32, device=dev)
             cnt = torch.zeros(1, dtype=torch.int64, device=dev)
-            tile = autotune(crys.OP_SELECT, lambda: crys.crys_select(x, n, -(1 << 31), datagen.select_threshold(0.5),
-                                                                      out, cnt, 0), args)
+            his = [datagen.select_threshold(i / 10) for i in range(11)]
+
+            def whole_sweep():  # the metric is the mean over the sweep, so tune on all of it
+                for hi in his:
+                    crys.crys_select(x, n, -(1 << 31), hi, out, cnt, 0)
+            tile = autotune(crys.OP_SELECT, whole_sweep, args)
             sweep = {}
             for sigma in [i / 10 for i in range(11)]:
                 hi = datagen.select_threshold(sigma)
@@ -498,6 +531,7 @@ def run_operator(args, rank, world, local):
             n_probe = args.rows or (1 << 28)
             fk_pay = None
             res = {}
+            l2_bytes = int(getattr(torch.cuda.get_device_properties(dev), "L2_cache_size", 126 << 20))
             for lg in args.join_sizes:
                 nb = 1 << lg
                 bk = dgd.perm_i32(seed, datagen.STREAMS["join.bkey"], nb, dev)
@@ -513,16 +547,25 @@ def run_operator(args, rank, world, local):
                                    args.steps, args.warmup, stream)
                 bms = time_launches(lambda: (crys.crys_hash_init(ht.struct), crys.crys_hash_build(bk, bv, nb, [], ht.struct)),
                                     max(1, args.steps // 2), 1, stream)
-                res[f"2^{lg}"] = {"probe_ms": round(statistics.median(ms), 4), "build_ms": round(statistics.median(bms), 4),
-                                  "table_mb": round(ht.nbytes / 2 ** 20, 3), "tile": tile}
+                pm = statistics.median(ms)
+                # Section 4.3 model: the probe scan plus one 32-byte sector per probe that
+                # misses L2 (hit share pi = L2 size / table size, at most 1)
+                pi = min(1.0, l2_bytes / ht.nbytes)
+                model = 8 * n_probe + (1.0 - pi) * n_probe * 32
+                res[f"2^{lg}"] = {"probe_ms": round(pm, 4), "build_ms": round(statistics.median(bms), 4),
+                                  "table_mb": round(ht.nbytes / 2 ** 20, 3), "tile": tile,
+                                  "model_bytes": int(model),
+                                  "model_frac": round(model / (pm / 1e3) / 1e9 / measured_hbm_peak()[0], 4)}
                 del ht, bk, bv, fk
-            # headline: the largest table (HBM-resident probes)
+            # headline: the largest table (HBM-resident probes), against the model's bytes
             last = res[f"2^{args.join_sizes[-1]}"]
-            alg = 8 * n_probe
+            alg = last["model_bytes"]
             line = op_line(args, world, "join", alg / (last["probe_ms"] / 1e3) / 1e9, "GB/s", "probe_kernel", alg,
                            last["probe_ms"], {"probe_rows": n_probe, "build_rows": f"2^{args.join_sizes[0]}..2^{args.join_sizes[-1]}",
                                               "fill": "50%", "l2": "probe side larger than L2"},
-                           {"sweep": res, "note": "algorithmic bytes = probe scan 8|P| only; slot reads are extra traffic"})
+                           {"sweep": res, "l2_bytes": l2_bytes,
+                            "note": "algorithmic bytes = probe scan 8|P| + (1 - pi)|P| 32-byte slot sectors, "
+                                    "pi = min(1, L2 / table) (Section 4.3 model)"})
         elif args.workload == "sort":
             n = args.rows or (1 << 28)
             keys = dgd.bits_i32(seed, datagen.STREAMS["sort.key"], n, dev)
@@ -538,7 +581,7 @@ def run_operator(args, rank, world, local):
                            {"tile": tile})
         elif args.workload == "q1":
             sizes = [args.rows] if args.rows else [1 << 22, 1 << 28]
-            results, tiles = {}, {}
+            results, tiles, graphed = {}, {}, {}
             flush_buf = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
             for n in sizes:
                 t = dgd.q1_tables(seed, n, dev)
@@ -553,13 +596,21 @@ def run_operator(args, rank, world, local):
                                    flush=lambda: l2_flush(flush_buf))
                 results[n] = statistics.median(ms)
                 tiles[n] = tile
+                graphed[n] = graph_differential_ms(lambda: crys.crys_run_plan(table, plan),
+                                                   lambda: l2_flush(flush_buf))
                 del t, f, d, ht, table, plan
             n = sizes[0]
             avg = results[n]
+            peak_gbs = measured_hbm_peak()[0]
             extra = {"by_rows": {str(k): {"ms": round(v, 4), "GB/s": round(16 * k / (v / 1e3) / 1e9, 1),
-                                          "frac": round(16 * k / (v / 1e3) / 1e9 / measured_hbm_peak()[0], 4),
+                                          "frac": round(16 * k / (v / 1e3) / 1e9 / peak_gbs, 4),
+                                          "graph_ms": round(graphed[k], 4),
+                                          "graph_frac": round(16 * k / (graphed[k] / 1e3) / 1e9 / peak_gbs, 4)
+                                          if graphed[k] > 0 else None,
                                           "tile": tiles[k]}
-                                 for k, v in results.items()}}
+                                 for k, v in results.items()},
+                     "graph_ms_note": "per-launch device time from CUDA-graph replays of k x {L2 flush, "
+                                      "kernel} minus k x {L2 flush}: no launch or event overhead"}
             line = op_line(args, world, "q1", 16 * n / (avg / 1e3) / 1e9, "GB/s", "plan_kernel", 16 * n, avg,
                            {"rows": n, "dtype": "int64", "l2": "flushed between timed launches (512 MB write)",
                             "query": "yr == 3 AND a < 25 AND 1 <= b <= 3, SUM(c * b), 2556-row date-like dimension"},
