@@ -240,6 +240,13 @@ __device__ __forceinline__ bool hash_find(const uint64_t* slots, const HashFn& f
   return hash_resolve(slots, f, h, ld_slot(slots + h, pol), key, value, pol);
 }
 
+// Fire-and-forget 64-bit add to global memory (no value returned, so the issuing warp
+// does not wait for it), with an L2 policy: accumulators that many rows update should
+// stay resident while the fact stream passes through L2.
+__device__ __forceinline__ void red_add_global(unsigned long long* p, unsigned long long v, uint64_t pol) {
+  asm volatile("red.global.add.L2::cache_hint.u64 [%0], %1, %2;" ::"l"(p), "l"(v), "l"(pol) : "memory");
+}
+
 // ---------------------------------------------------------------- scans / reductions
 
 __device__ __forceinline__ int32_t warp_inclusive_scan(int32_t v, int lane) {

@@ -466,8 +466,8 @@ __global__ void __launch_bounds__(THREADS) plan_kernel(const __grid_constant__ P
         atomicAdd(acc.sums + gid[i], static_cast<unsigned long long>(val[i]));
         atomicAdd(acc.counts + gid[i], 1u);
       } else {
-        atomicAdd(q.sums + gid[i], static_cast<unsigned long long>(val[i]));
-        if (q.counts) atomicAdd(q.counts + gid[i], 1ull);
+        red_add_global(q.sums + gid[i], static_cast<unsigned long long>(val[i]), pol_table);
+        if (q.counts) red_add_global(q.counts + gid[i], 1ull, pol_table);
       }
     }
   }
@@ -628,8 +628,8 @@ __global__ void __launch_bounds__(THREADS, (24 * kWarp) / THREADS > 0 ? (24 * kW
             atomicAdd(acc.sums + q.acc_off + gid[i], static_cast<unsigned long long>(val[i]));
             atomicAdd(acc.counts + q.acc_off + gid[i], 1u);
           } else {
-            atomicAdd(q.sums + gid[i], static_cast<unsigned long long>(val[i]));
-            if (q.counts) atomicAdd(q.counts + gid[i], 1ull);
+            red_add_global(q.sums + gid[i], static_cast<unsigned long long>(val[i]), pol_table);
+            if (q.counts) red_add_global(q.counts + gid[i], 1ull, pol_table);
           }
         }
       }
@@ -796,8 +796,9 @@ __device__ __forceinline__ void finish_pair(const int32_t* D, const int32_t* con
         (static_cast<uint64_t>(static_cast<uint32_t>(ptrs.y)) << 32) | static_cast<uint32_t>(ptrs.x));
     unsigned long long* counts = reinterpret_cast<unsigned long long*>(
         (static_cast<uint64_t>(static_cast<uint32_t>(ptrs.w)) << 32) | static_cast<uint32_t>(ptrs.z));
-    atomicAdd(sums + gid, static_cast<unsigned long long>(val));
-    if (counts) atomicAdd(counts + gid, 1ull);
+    const uint64_t keep = policy_evict_last();
+    red_add_global(sums + gid, static_cast<unsigned long long>(val), keep);
+    if (counts) red_add_global(counts + gid, 1ull, keep);
   }
 }
 
