@@ -808,7 +808,7 @@ __device__ __forceinline__ void finish_pair(const int32_t* D, const int32_t* con
 template <int THREADS, int ITEMS>
 struct TagSmem {
   static constexpr int TILE = THREADS * ITEMS;
-  static constexpr int LIST = kWarp * CRYS_MAX_PLANS;  // one row per lane, every query
+  static constexpr int LIST = 256;  // list window of a warp (a round averages a few per lane)
   static constexpr size_t desc_bytes = CRYS_MAX_PLANS * kDescWords * 4;
   static constexpr size_t cols_off = (desc_bytes + 15) / 16 * 16;
   static constexpr size_t pv_off = cols_off + CRYS_MAX_COLS * 8;
@@ -899,17 +899,24 @@ __device__ __forceinline__ void tagged_scan_body(const TagArgs& a) {
       const int total = __shfl_sync(0xFFFFFFFFu, incl, kWarp - 1);
       if (total == 0) continue;
       const int r = ((i >> 2) * THREADS + tid) * 4 + (i & 3);
-      int k = incl - n;
-      for (uint32_t m = rm[i]; m; m &= m - 1) list[k++] = static_cast<uint16_t>(((__ffs(m) - 1) << 11) | r);
-      __syncwarp();
-      for (int base = 0; base < total; base += kWarp) {
-        if (base + lane < total) {
-          const uint32_t ent = list[base + lane];
-          const int rr = static_cast<int>(ent & 0x7FFu);
-          finish_pair<TILE>(desc + (ent >> 11) * kDescWords, scols, row0 + rr, rr, pv, acc, a.err);
+      // the pairs go through the list in windows of L::LIST entries (one window unless
+      // the round expands more pairs than that)
+      for (int w0 = 0; w0 < total; w0 += L::LIST) {
+        int k = incl - n;
+        for (uint32_t m = rm[i]; m; m &= m - 1, ++k)
+          if (k >= w0 && k < w0 + L::LIST)
+            list[k - w0] = static_cast<uint16_t>(((__ffs(m) - 1) << 11) | r);
+        __syncwarp();
+        const int wn = (total - w0) < L::LIST ? (total - w0) : L::LIST;
+        for (int base = 0; base < wn; base += kWarp) {
+          if (base + lane < wn) {
+            const uint32_t ent = list[base + lane];
+            const int rr = static_cast<int>(ent & 0x7FFu);
+            finish_pair<TILE>(desc + (ent >> 11) * kDescWords, scols, row0 + rr, rr, pv, acc, a.err);
+          }
         }
+        __syncwarp();  // the list is reused by the next window or item slot
       }
-      __syncwarp();  // the list is reused by the next item slot
     }
   }
   __syncthreads();

@@ -170,3 +170,19 @@ def test_untaggable_batch_falls_back(crys, orc, world):
     for (joins, preds, agg), (ss, cc) in zip(qs, outs):
         rs, rc = orc.run_plan_raw(world["fact"], preds, [o for _, o in joins], agg)
         assert np.array_equal(ss.cpu().numpy(), rs)
+
+
+def test_tagged_every_row_expands_every_query(crys, orc, world):
+    # 32 queries without dimension filters: every row expands 32 (row, query) pairs, so a
+    # warp's round holds 1024 of them and goes through the list in several windows
+    qs = []
+    for i in range(32):
+        joins = [] if i % 3 else [((0, world["t0"], 16, X, []),
+                                   {"fk_col": 0, "keys": world["d0"]["key"], "preds": [],
+                                    "group": world["d0"]["x"], "card": 16})]
+        qs.append((joins, [(2, 1, 50 - i)], ("sum", 4, None) if i % 2 else ("mul", 4, 3)))
+    plans, outs = _plans(crys, qs)
+    _tagged(crys, world, plans)
+    for (joins, preds, agg), (s, c) in zip(qs, outs):
+        rs, rc = orc.run_plan_raw(world["fact"], preds, [o for _, o in joins], agg)
+        assert np.array_equal(s.cpu().numpy(), rs) and np.array_equal(c.cpu().numpy(), rc)
