@@ -116,8 +116,12 @@ def dist_setup(args):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
         import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl" if args.impl != "reference" else "gloo")
+        # NCCL between the GPUs of our arm; gloo for the host-only reference arm (and
+        # wherever no GPU is visible)
+        gpu = args.impl != "reference" and torch.cuda.is_available()
+        if gpu:
+            torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if gpu else "gloo")
     elif torch.cuda.is_available():
         torch.cuda.set_device(0)
     return rank, world, local
@@ -134,7 +138,8 @@ def max_over_ranks(x: float, world: int) -> float:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
