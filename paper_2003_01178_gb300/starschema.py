@@ -27,10 +27,10 @@ from dataclasses import dataclass, field
 
 import torch
 
-from . import (HashTable, crys_hash_build, crys_hash_init, crys_pack_fields, crys_run_plan,
+from . import (HashTable, crys_get_tile, crys_hash_build, crys_hash_init, crys_pack_fields, crys_run_plan,
                crys_run_plans_tagged, crys_run_plans_tagged_bytes, crys_tagged_block_bytes,
                crys_tagged_launch, crys_tagged_prepare, make_plan, make_table, capacity_for,
-               ACCUMULATE, MAX_PLANS, HASH_DIRECT, HASH_IDENT, OK, TAG_ANNOTATE)
+               ACCUMULATE, MAX_PLANS, HASH_DIRECT, HASH_IDENT, OK, OP_SHARED_SCAN, TAG_ANNOTATE)
 
 
 @dataclass
@@ -231,6 +231,7 @@ class ReplayedScan:
         self.dev_block = torch.empty(nb, dtype=torch.uint8, device=store.device)
         self.host = [torch.empty(nb, dtype=torch.uint8, pin_memory=True) for _ in range(2)]
         self.graphs = [None, None]
+        self.shape = None    # tile shape the graphs were captured with
         self.done = [None, None]
         self.k = 0
         self.replays = 0
@@ -261,6 +262,13 @@ class ReplayedScan:
                                  scratch.numel(), self.host[i].data_ptr())
         if rc != OK:
             return False
+        shape = crys_get_tile(OP_SHARED_SCAN)
+        if shape != self.shape:                 # a new tile shape: capture both graphs again
+            for j in range(2):
+                if self.done[j] is not None:
+                    self.done[j].synchronize()
+            self.graphs = [None, None]
+            self.shape = shape
         if self.graphs[i] is None:
             self._capture(i)
         with torch.cuda.stream(self.stream):

@@ -105,3 +105,29 @@ def test_block_for_another_tile_shape_is_refused(store):
     crys.crys_set_tile(crys.OP_SHARED_SCAN, 0)
     assert crys.crys_device_errors(clear=True) & crys.DEV_BOUNDS
     assert torch.equal(cq.sums, torch.zeros_like(before))   # cleared by the prepare kernel only
+
+
+def test_replayed_scan_follows_a_new_tile_shape(store, orc):
+    """Graphs captured under one tile shape are captured again when the shape changes
+    (as the autotuner may do between launches); results stay exact."""
+    import paper_2003_01178_gb300 as crys
+    from paper_2003_01178_gb300.starschema import ReplayedScan
+    host, ss = store
+    queries = [datagen.ss_query(25, q) for q in range(10)]
+    stream = torch.cuda.Stream()
+    rep = ReplayedScan(ss, stream)
+    with torch.cuda.stream(stream):
+        mine = [ss.compile(q, zero=False) for q in queries]
+    n = ss.n_rows
+    try:
+        crys.crys_set_tile(crys.OP_SHARED_SCAN, 0)
+        assert rep.launch(mine, 0, 100_000, list(range(10)))
+        crys.crys_set_tile(crys.OP_SHARED_SCAN, 1)
+        assert rep.launch(mine, 100_000, n, [])
+        stream.synchronize()
+    finally:
+        crys.crys_set_tile(crys.OP_SHARED_SCAN, 0)
+    assert crys.crys_device_errors(clear=True) == 0
+    for c, q in zip(mine, queries):
+        rs, rc = orc.ss_run(host, q)
+        assert np.array_equal(c.sums.cpu().numpy(), rs) and np.array_equal(c.counts.cpu().numpy(), rc)
