@@ -730,7 +730,9 @@ struct TagScanPair {
   uint32_t nonjoin;
 };
 
-struct TagArgs {
+// Everything a tagged scan launch needs except the query descriptors (TagHead), and the
+// descriptors after it (TagArgs).
+struct TagHead {
   const int32_t* cols[CRYS_MAX_COLS];
   uint32_t col_mask;  // fact columns the batch reads
   int64_t row_begin, row_end;
@@ -742,6 +744,9 @@ struct TagArgs {
   int32_t smem_bytes;  // dynamic shared memory the launch provides
   int32_t* err;
   TagScanPair pairs[kMaxTagPairs];
+};
+
+struct TagArgs : TagHead {
   int32_t desc[CRYS_MAX_PLANS * kDescWords];
 };
 
@@ -817,7 +822,7 @@ struct TagSmem {
 };
 
 template <int THREADS, int ITEMS>
-__device__ __forceinline__ void tagged_scan_body(const TagArgs& a) {
+__device__ __forceinline__ void tagged_scan_body(const TagHead& a, const int32_t* desc_src) {
   using L = TagSmem<THREADS, ITEMS>;
   constexpr int TILE = L::TILE;
   constexpr int VEC = ITEMS / 4;
@@ -838,7 +843,7 @@ __device__ __forceinline__ void tagged_scan_body(const TagArgs& a) {
     return;
   }
   const SharedAcc acc = shared_acc(smem_raw + L::acc_off(a.n_pairs), a.shared_groups);
-  for (int w = tid; w < a.n_queries * kDescWords; w += THREADS) desc[w] = a.desc[w];
+  for (int w = tid; w < a.n_queries * kDescWords; w += THREADS) desc[w] = desc_src[w];
   if (tid < CRYS_MAX_COLS) scols[tid] = a.cols[tid];
   for (int g = tid; g < a.shared_groups; g += THREADS) {
     acc.sums[g] = 0;
@@ -936,7 +941,14 @@ __device__ __forceinline__ void tagged_scan_body(const TagArgs& a) {
 template <int THREADS, int ITEMS>
 __global__ void __launch_bounds__(THREADS, (24 * kWarp) / THREADS > 0 ? (24 * kWarp) / THREADS : 1)
     tagged_scan_kernel(const __grid_constant__ TagArgs a) {
-  tagged_scan_body<THREADS, ITEMS>(a);
+  // the head is read on every tile: a shared-memory copy is cheaper than the parameter
+  // bank, whose cache does not hold a 9 KB argument block
+  __shared__ __align__(16) TagHead head;
+  static_assert(sizeof(TagHead) % 4 == 0, "copied as 32-bit words");
+  for (int w = threadIdx.x; w < static_cast<int>(sizeof(TagHead) / 4); w += THREADS)
+    reinterpret_cast<uint32_t*>(&head)[w] = reinterpret_cast<const uint32_t*>(&a)[w];
+  __syncthreads();
+  tagged_scan_body<THREADS, ITEMS>(head, a.desc);
 }
 
 // ------------------------------------------------------------------ graph-replayable launch
@@ -975,7 +987,13 @@ __global__ void __launch_bounds__(256) prepare_kernel(const TagLaunch* __restric
 template <int THREADS, int ITEMS>
 __global__ void __launch_bounds__(THREADS, (24 * kWarp) / THREADS > 0 ? (24 * kWarp) / THREADS : 1)
     tagged_scan_kernel_dev(const TagArgs* __restrict__ a) {
-  tagged_scan_body<THREADS, ITEMS>(*a);
+  // the head is read on every tile: one shared-memory copy per block
+  __shared__ __align__(16) TagHead head;
+  static_assert(sizeof(TagHead) % 4 == 0, "copied as 32-bit words");
+  for (int w = threadIdx.x; w < static_cast<int>(sizeof(TagHead) / 4); w += THREADS)
+    reinterpret_cast<uint32_t*>(&head)[w] = reinterpret_cast<const uint32_t*>(a)[w];
+  __syncthreads();
+  tagged_scan_body<THREADS, ITEMS>(head, a->desc);
 }
 
 // ------------------------------------------------------------------ packing
