@@ -355,14 +355,22 @@ def served_loop(store, args, rank):
     server = QueryServer(store, segments=args.segments, max_slots=BATCH, memory_budget=16 << 30)
     # closed loop: every request queued at t=0 (throughput)
     _, st_closed = server.serve(queries, np.zeros(n), realtime=False)
-    # open loop: Poisson arrivals at 70% of the closed-loop rate (latency)
+    # open loop: Poisson arrivals at 70% of the closed-loop rate (latency), and the
+    # latency at a few other offered loads
     rate = max(1.0, 0.7 * st_closed.qps)
     arrivals = datagen.ss_arrivals(args.seed, n, rate)
     _, st_open = server.serve(queries, arrivals, realtime=True)
+    curve = []
+    for load in (0.3, 0.5, 0.9):
+        r = max(1.0, load * st_closed.qps)
+        _, st = server.serve(queries, datagen.ss_arrivals(args.seed + 1, n, r), realtime=True)
+        curve.append({"offered_qps": round(r, 1), "served_qps": round(st.qps, 1),
+                      "p50_ms": round(st.percentile_ms(50), 2), "p99_ms": round(st.percentile_ms(99), 2)})
     groups = sum(store.groups(q) for q in queries)
     return {"closed_loop_qps": round(st_closed.qps, 2), "open_loop_offered_qps": round(rate, 2),
             "open_loop_qps": round(st_open.qps, 2),
             "p50_ms": round(st_open.percentile_ms(50), 3), "p99_ms": round(st_open.percentile_ms(99), 3),
+            "latency_by_load": curve,
             "closed_loop_p50_ms": round(st_closed.percentile_ms(50), 3),
             "closed_loop_p99_ms": round(st_closed.percentile_ms(99), 3),
             "queries": n, "segments": args.segments, "max_active": st_open.max_active,
