@@ -281,7 +281,7 @@ __device__ __forceinline__ uint32_t eval_shared(const DevQuery& q, const CachedC
 // query reads is loaded for all rows (no selective loads and no per-group branches);
 // predicates only clear bits of the row bitmap and dead rows contribute 0.
 template <int THREADS, int ITEMS>
-__device__ __forceinline__ uint32_t eval_eager(const DevQuery& q, const GlobalCols& cols, uint32_t alive,
+__device__ __forceinline__ uint32_t eval_eager_loop(const DevQuery& q, const GlobalCols& cols, uint32_t alive,
                                                int32_t (&gid)[ITEMS], int64_t (&val)[ITEMS],
                                                int32_t* err, uint64_t pol_table) {
   constexpr int VEC = ITEMS / 4;
@@ -351,6 +351,103 @@ __device__ __forceinline__ uint32_t eval_eager(const DevQuery& q, const GlobalCo
   return alive;
 }
 
+// The same evaluation with every column load of the tile issued before any value is
+// used (up to two fact predicates, up to four joins' foreign keys and the aggregate
+// operands), so that one L2 round trip serves the tile instead of one per step; for
+// tiles of at most 4 rows per thread, where the loaded vectors fit in registers.
+template <int THREADS, int ITEMS>
+__device__ __forceinline__ uint32_t eval_eager_preload(const DevQuery& q, const GlobalCols& cols, uint32_t alive,
+                                                       int32_t (&gid)[ITEMS], int64_t (&val)[ITEMS],
+                                                       int32_t* err, uint64_t pol_table) {
+  static_assert(ITEMS == 4, "one 16-byte vector per column and thread");
+  constexpr int KP = 2;
+  const int p = static_cast<int>(threadIdx.x) * 4;
+  int4 pv[KP], kv[CRYS_MAX_JOINS];
+#pragma unroll
+  for (int f = 0; f < KP; ++f) pv[f] = f < q.n_preds ? cols.load4(q.pred_col[f], p) : make_int4(0, 0, 0, 0);
+#pragma unroll
+  for (int jn = 0; jn < CRYS_MAX_JOINS; ++jn)
+    kv[jn] = jn < q.n_joins ? cols.load4(q.joins[jn].fk_col, p) : make_int4(0, 0, 0, 0);
+  const int4 av = cols.load4(q.agg_a, p);
+  const int4 bv = q.agg_op != CRYS_AGG_A ? cols.load4(q.agg_b, p) : make_int4(0, 0, 0, 0);
+#pragma unroll
+  for (int f = 0; f < KP; ++f) {
+    if (f >= q.n_preds) break;
+    int32_t v[4];
+    unpack4(pv[f], v);
+    const int32_t lo = q.pred_lo[f];
+    const uint32_t span = q.pred_span[f];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) alive &= ~(static_cast<uint32_t>(!in_span(v[e], lo, span)) << e);
+  }
+  for (int f = KP; f < q.n_preds; ++f) {
+    int32_t v[4];
+    unpack4(cols.load4(q.pred_col[f], p), v);
+    const int32_t lo = q.pred_lo[f];
+    const uint32_t span = q.pred_span[f];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) alive &= ~(static_cast<uint32_t>(!in_span(v[e], lo, span)) << e);
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) gid[i] = 0;
+#pragma unroll
+  for (int jn = 0; jn < CRYS_MAX_JOINS; ++jn) {
+    if (jn >= q.n_joins) break;
+    const DevJoin& J = q.joins[jn];
+    int32_t key[4], value[4];
+    unpack4(kv[jn], key);
+    alive &= probe_items<4>(J.slots, J.hash, key, alive, value, pol_table);
+    for (int f = 0; f < J.n_fp; ++f) {
+      const uint32_t sh = J.fp_shift[f], mk = J.fp_mask[f], span = J.fp_span[f];
+      const int32_t lo = J.fp_lo[f];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) alive &= ~(static_cast<uint32_t>(!in_span(field_of(value[i], sh, mk), lo, span)) << i);
+    }
+    if (J.card > 0) {
+      const uint32_t card = static_cast<uint32_t>(J.card);
+      uint32_t bad = 0;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const uint32_t code = static_cast<uint32_t>(field_of(value[i], J.gshift, J.gmask));
+        bad |= static_cast<uint32_t>(code >= card) << i;
+        gid[i] += static_cast<int32_t>(code) * J.stride;
+      }
+      bad &= alive;
+      if (bad) {
+        set_error(err, CRYS_DEV_BAD_GROUP);
+        alive &= ~bad;
+      }
+    }
+  }
+  int32_t va[4], vb[4];
+  unpack4(av, va);
+  unpack4(bv, vb);
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const int64_t x = va[e], y = vb[e];
+    int64_t r;
+    switch (q.agg_op) {
+      case CRYS_AGG_A_MUL_B: r = x * y; break;
+      case CRYS_AGG_A_SUB_B: r = x - y; break;
+      case CRYS_AGG_A_ADD_B: r = x + y; break;
+      default: r = x; break;
+    }
+    val[e] = ((alive >> e) & 1u) ? r : 0;
+  }
+  return alive;
+}
+
+template <int THREADS, int ITEMS, bool PRELOAD>
+__device__ __forceinline__ uint32_t eval_eager(const DevQuery& q, const GlobalCols& cols, uint32_t alive,
+                                               int32_t (&gid)[ITEMS], int64_t (&val)[ITEMS],
+                                               int32_t* err, uint64_t pol_table) {
+  if constexpr (PRELOAD && ITEMS == 4) {
+    return eval_eager_preload<THREADS, ITEMS>(q, cols, alive, gid, val, err, pol_table);
+  } else {
+    return eval_eager_loop<THREADS, ITEMS>(q, cols, alive, gid, val, err, pol_table);
+  }
+}
+
 // Rows of this thread that exist in a tile with `valid` rows.
 template <int THREADS, int ITEMS>
 __device__ __forceinline__ uint32_t rows_present(int valid) {
@@ -415,7 +512,7 @@ __device__ __forceinline__ void prefetch_tile(const int32_t* const* cols, uint32
 constexpr int kPrefetchTiles = 2;  // tiles of a block prefetched ahead of the one in work
 constexpr int kTagPrefetchTiles = 1;  // the same for the tagged scan, whose tiles stay in work longer
 
-template <int THREADS, int ITEMS>
+template <int THREADS, int ITEMS, bool PRELOAD>
 __global__ void __launch_bounds__(THREADS) plan_kernel(const __grid_constant__ PlanArgs a) {
   constexpr int TILE = THREADS * ITEMS;
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -450,7 +547,7 @@ __global__ void __launch_bounds__(THREADS) plan_kernel(const __grid_constant__ P
     int32_t gid[ITEMS];
     int64_t val[ITEMS];
     const uint32_t alive = q.never ? 0u
-                                   : eval_eager<THREADS, ITEMS>(q, cols, rows_present<THREADS, ITEMS>(cols.valid),
+                                   : eval_eager<THREADS, ITEMS, PRELOAD>(q, cols, rows_present<THREADS, ITEMS>(cols.valid),
                                                                 gid, val, a.err, pol_table);
     if (q.acc_mode == kAccSingle) {
 #pragma unroll
@@ -1157,10 +1254,19 @@ int launch_plan(PlanArgs& a, cudaStream_t s) {
   } else {
     a.q.acc_mode = kAccGlobal;
   }
-  auto k = plan_kernel<THREADS, ITEMS>;
-  if (!allow_smem(k, smem)) return CRYS_ECUDA;
+  // With few tiles per block the kernel waits on each tile's loads in turn: then all of
+  // a tile's loads go out together (4-row tiles only); with many tiles per block the
+  // lighter looping evaluation keeps more blocks resident.
   const int64_t ntiles = (a.row_end - a.row_begin + TILE - 1) / TILE;
-  const int grid = persistent_grid(k, THREADS, smem, ntiles);
+  auto kl = plan_kernel<THREADS, ITEMS, false>;
+  if (!allow_smem(kl, smem)) return CRYS_ECUDA;
+  int grid = persistent_grid(kl, THREADS, smem, ntiles);
+  const bool preload = ITEMS == 4 && ntiles <= 8 * static_cast<int64_t>(grid);
+  auto k = preload ? plan_kernel<THREADS, ITEMS, true> : kl;
+  if (preload) {
+    if (!allow_smem(k, smem)) return CRYS_ECUDA;
+    grid = persistent_grid(k, THREADS, smem, ntiles);
+  }
   if (!counts_fit(a.row_end - a.row_begin, grid)) return CRYS_EINVAL;
   k<<<grid, THREADS, smem, s>>>(a);
   note_launch();

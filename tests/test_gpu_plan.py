@@ -36,7 +36,7 @@ def _q1_gpu(crys, fact, dim, year=3):
     return int(sums[0].item()), int(counts[0].item())
 
 
-@pytest.mark.parametrize("n", [0, 1, 5, 1023, 4096, 4099, 100_003, 1 << 22])
+@pytest.mark.parametrize("n", [0, 1, 5, 1023, 4096, 4099, 100_003, 1 << 22, (1 << 24) + 3])
 @pytest.mark.parametrize("variant", range(4))
 def test_q1_parity(crys, orc, n, variant):
     crys.crys_set_tile(crys.OP_PLAN, variant)
