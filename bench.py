@@ -536,10 +536,24 @@ def run_operator(args, rank, world, local):
                 sweep[f"{sigma:.1f}"] = statistics.median(ms)
             avg = statistics.mean(sweep.values())
             alg = statistics.mean([4 * n * (1 + float(s)) for s in sweep])
+            # the independent-threads selection the paper compares against (ablation)
+            stb = crys.crys_select_strawman(None, n, -(1 << 31), 0, None, None, None, -1)
+            stemp = crys.scratch(stb, dev)
+            straw = {}
+            for sigma in (0.0, 0.5, 1.0):
+                hi = datagen.select_threshold(sigma)
+                ms = time_launches(lambda: crys.crys_select_strawman(x, n, -(1 << 31), hi, out, cnt, stemp, stb),
+                                   args.steps, args.warmup, stream)
+                straw[f"{sigma:.1f}"] = round(statistics.median(ms), 4)
+            strawman = {"ms": straw,
+                        "tile_over_independent_at_0.5": round(straw["0.5"] / sweep["0.5"], 2),
+                        "paper": "19 ms independent threads vs 2.1 ms tile-based, V100, 2^29 rows, sigma 0.5 "
+                                 "(Section 3.2)"}
             line = op_line(args, world, "select", alg / (avg / 1e3) / 1e9, "GB/s", "select_kernel", alg, avg,
                            {"rows": n, "selectivity": "0.0..1.0 step 0.1 (mean over the sweep)",
                             "l2": "inputs larger than L2"},
-                           {"sweep_ms": {k: round(v, 4) for k, v in sweep.items()}, "tile": tile})
+                           {"sweep_ms": {k: round(v, 4) for k, v in sweep.items()}, "tile": tile,
+                            "independent_threads": strawman})
         elif args.workload == "project":
             n = args.rows or (1 << 29)
             x1 = dgd.uniform_f32(seed, datagen.STREAMS["proj.x1"], n, dev)

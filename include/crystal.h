@@ -101,6 +101,15 @@ int crys_select(const int32_t* x, int64_t n, int32_t lo, int32_t hi, int32_t* ou
 int crys_select_static(const int32_t* x, int64_t n, int32_t lo, int32_t hi, int32_t* out,
                        int64_t* d_count, crys_stream s);
 
+/* The "independent threads" selection the paper compares the tile model against
+ * (Section 3.2, Figure "tile"): each thread of a fixed launch owns a contiguous chunk of
+ * x; one kernel counts each thread's matches, one scans the counts, one re-reads the
+ * chunks and writes the matches.  Same result as crys_select with order_preserving = 1
+ * (input order); kept as an ablation.  Scratch: one int64 per launched thread, two-call
+ * size query as in crys_select (d_temp NULL: *temp_bytes receives the size). */
+int crys_select_strawman(const int32_t* x, int64_t n, int32_t lo, int32_t hi, int32_t* out,
+                         int64_t* d_count, void* d_temp, size_t* temp_bytes, crys_stream s);
+
 /* ------------------------------------------------------------------ projection
  * Section 4.1, queries Q1 and Q2: y = a*x1 + b*x2 (CRYS_PROJ_LINEAR) or the sigmoid
  * 1/(1 + exp(-(a*x1 + b*x2))) (CRYS_PROJ_SIGMOID), float32 in and out, one rounding per

@@ -92,6 +92,7 @@ def lib():
         L.crys_launch_count.restype = i64
         L.crys_select.argtypes = [p, i64, i32, i32, p, p, C.c_int, p, sz, p]
         L.crys_select_static.argtypes = [p, i64, i32, i32, p, p, p]
+        L.crys_select_strawman.argtypes = [p, i64, i32, i32, p, p, p, sz, p]
         L.crys_project.argtypes = [p, p, i64, C.c_float, C.c_float, C.c_int, p, p]
         L.crys_hash_init.argtypes = [C.POINTER(crys_hash), p]
         L.crys_hash_build.argtypes = [p, p, i64, C.POINTER(crys_pred), i32, C.POINTER(crys_hash), p]
@@ -114,7 +115,8 @@ def lib():
         L.crys_tile_variants.argtypes = [C.c_int, C.POINTER(C.c_int32), C.POINTER(C.c_int32), i32]
         L.crys_set_tile.argtypes = [C.c_int, i32]
         L.crys_get_tile.argtypes = [C.c_int]
-        for fn in ("crys_device_errors", "crys_select", "crys_select_static", "crys_project", "crys_hash_init",
+        for fn in ("crys_device_errors", "crys_select", "crys_select_static", "crys_select_strawman",
+                   "crys_project", "crys_hash_init",
                    "crys_hash_build", "crys_probe_aggregate", "crys_sort", "crys_plan_groups",
                    "crys_pack_fields",
                    "crys_run_plan", "crys_run_plans", "crys_run_plans_tagged_bytes",
@@ -183,6 +185,21 @@ def crys_select_static(x, n: int, lo: int, hi: int, out, d_count, stream=None) -
     (no allocation on the call path; n <= 2^25)."""
     _check(lib().crys_select_static(_ptr(x), n, lo, hi, _ptr(out), _ptr(d_count), _stream(stream)),
            "crys_select_static")
+
+
+def crys_select_strawman(x, n: int, lo: int, hi: int, out, d_count, d_temp=None, temp_bytes: int | None = None,
+                         stream=None) -> int:
+    """The independent-threads selection (ablation).  Returns the scratch size when
+    d_temp is None and temp_bytes is -1."""
+    if d_temp is None and temp_bytes == -1:
+        size = C.c_size_t(0)
+        _check(lib().crys_select_strawman(None, n, lo, hi, None, None, None, C.byref(size), None),
+               "crys_select_strawman")
+        return size.value
+    tb = C.c_size_t(temp_bytes if temp_bytes is not None else 0)
+    _check(lib().crys_select_strawman(_ptr(x), n, lo, hi, _ptr(out), _ptr(d_count), _ptr(d_temp), C.byref(tb),
+                                      _stream(stream)), "crys_select_strawman")
+    return 0
 
 
 def crys_project(x1, x2, n: int, a: float, b: float, op: int, y, stream=None) -> None:

@@ -250,3 +250,20 @@ def test_device_generator_matches_host(crys):
     big = dgd.uniform_i32(4, 5, 1 << 24, 0, I32_MAX).cpu().numpy()
     idx = np.array([0, 1, 12345, (1 << 24) - 1])
     assert np.array_equal(big[idx], datagen.uniform_i32_at(4, 5, idx, 0, I32_MAX))
+
+
+@pytest.mark.parametrize("n", [0, 1, 5, 4097, 1_000_003, 1 << 22])
+@pytest.mark.parametrize("sigma", [0.0, 0.3, 1.0])
+def test_select_strawman_parity(crys, orc, n, sigma):
+    # the independent-threads selection: input order, like the order-preserving mode
+    x = datagen.uniform_i32(17 + n, datagen.STREAMS["sel.x"], n, 0, I32_MAX)
+    hi = datagen.select_threshold(sigma)
+    xd = _dev(x)
+    out = torch.empty(max(1, n), dtype=torch.int32, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    tb = crys.crys_select_strawman(None, n, I32_MIN, hi, None, None, None, -1)
+    temp = crys.scratch(tb, "cuda")
+    crys.crys_select_strawman(xd, n, I32_MIN, hi, out, cnt, temp, tb)
+    ref = orc.select(x, I32_MIN, hi)
+    c = int(cnt.item())
+    assert c == ref.size and np.array_equal(out[:c].cpu().numpy(), ref)
