@@ -16,6 +16,8 @@
 // because each thread kept a 2^r histogram in registers; the per-warp shared-memory
 // multisplit used here keeps 8-bit stable passes.  Signed order: the top digit has its
 // sign bit flipped.
+#include <type_traits>
+
 #include "common.cuh"
 #include "pipeline.cuh"
 #include "tiles.h"
@@ -101,7 +103,7 @@ struct PassArgs {
   int32_t* err;
 };
 
-template <int THREADS, int ITEMS>
+template <int THREADS, int ITEMS, int PASS>
 __global__ void __launch_bounds__(THREADS) sort_pass_kernel(PassArgs a) {
   constexpr int WARPS = THREADS / kWarp;
   constexpr int TILE = THREADS * ITEMS;
@@ -158,26 +160,34 @@ __global__ void __launch_bounds__(THREADS) sort_pass_kernel(PassArgs a) {
   const uint32_t lt_mask = (1u << lane) - 1u;
   int32_t key[ITEMS];
   uint32_t rank[ITEMS];
+  // a full tile (all but possibly the last) ranks without per-item bounds predicates
+  auto rank_items = [&](auto full_tag) {
+    constexpr bool FULL = decltype(full_tag)::value;
 #pragma unroll
-  for (int i = 0; i < ITEMS; ++i) {
-    const int pos = warp * WSEG + i * kWarp + lane;
-    const bool real = pos < valid;
-    key[i] = real ? skeys[pos] : 0;
-    const uint32_t d = real ? digit_of(key[i], a.pass) : 0u;
-    uint32_t peers = __ballot_sync(0xFFFFFFFFu, real);
+    for (int i = 0; i < ITEMS; ++i) {
+      const int pos = warp * WSEG + i * kWarp + lane;
+      const bool real = FULL || pos < valid;
+      key[i] = real ? skeys[pos] : 0;
+      const uint32_t d = real ? digit_of(key[i], PASS) : 0u;
+      uint32_t peers = FULL ? 0xFFFFFFFFu : __ballot_sync(0xFFFFFFFFu, real);
 #pragma unroll
-    for (int b = 0; b < 8; ++b) {
-      const uint32_t bit = (d >> b) & 1u;
-      const uint32_t vote = __ballot_sync(0xFFFFFFFFu, bit);
-      peers &= bit ? vote : ~vote;
+      for (int b = 0; b < 8; ++b) {
+        const uint32_t bit = (d >> b) & 1u;
+        const uint32_t vote = __ballot_sync(0xFFFFFFFFu, bit);
+        peers &= bit ? vote : ~vote;
+      }
+      uint32_t before = 0;
+      if (real) before = whist[warp][d];
+      __syncwarp();
+      rank[i] = before + __popc(peers & lt_mask);
+      if (real && (peers & lt_mask) == 0) whist[warp][d] = before + __popc(peers);
+      __syncwarp();
     }
-    uint32_t before = 0;
-    if (real) before = whist[warp][d];
-    __syncwarp();
-    rank[i] = before + __popc(peers & lt_mask);
-    if (real && (peers & lt_mask) == 0) whist[warp][d] = before + __popc(peers);
-    __syncwarp();
-  }
+  };
+  if (valid == TILE)
+    rank_items(std::true_type{});
+  else
+    rank_items(std::false_type{});
   __syncthreads();
 
   // Per digit: exclusive offsets of the warps and the tile's count.
@@ -236,6 +246,12 @@ __global__ void __launch_bounds__(THREADS) sort_pass_kernel(PassArgs a) {
       if (!failed) st_relaxed_u32(st, kFlagInclusive | (excl + count));
     }
     out_shift[tid] = static_cast<int32_t>(a.digit_base[tid] + excl - tile_start[tid]);
+    // the digit's run [start, start + count) of this tile must land inside the output
+    const int64_t start = static_cast<int64_t>(a.digit_base[tid]) + excl;
+    if (!failed && count && (start < 0 || start + count > a.n)) {
+      set_error(a.err, CRYS_DEV_BOUNDS);
+      failed = true;
+    }
   }
   if (__syncthreads_or(failed)) return;
 
@@ -245,7 +261,7 @@ __global__ void __launch_bounds__(THREADS) sort_pass_kernel(PassArgs a) {
   for (int i = 0; i < ITEMS; ++i) {
     const int pos = warp * WSEG + i * kWarp + lane;
     if (pos < valid) {
-      const uint32_t d = digit_of(key[i], a.pass);
+      const uint32_t d = digit_of(key[i], PASS);
       rank[i] += tile_start[d] + whist[warp][d];
       skeys[rank[i]] = key[i];
     }
@@ -265,13 +281,9 @@ __global__ void __launch_bounds__(THREADS) sort_pass_kernel(PassArgs a) {
   // BlockStore in sorted order: each digit run is written with consecutive addresses.
   for (int i = tid; i < valid; i += THREADS) {
     const int32_t k = skeys[i];
-    const int64_t g = static_cast<int64_t>(out_shift[digit_of(k, a.pass)]) + i;
-    if (g >= 0 && g < a.n) {
-      a.keys_out[g] = k;
-      a.vals_out[g] = svals[i];
-    } else {
-      set_error(a.err, CRYS_DEV_BOUNDS);
-    }
+    const int64_t g = static_cast<int64_t>(out_shift[digit_of(k, PASS)]) + i;  // checked per digit above
+    a.keys_out[g] = k;
+    a.vals_out[g] = svals[i];
   }
 }
 
@@ -317,8 +329,11 @@ int run_passes(const int32_t* keys_in, const int32_t* vals_in, int32_t* keys_out
   constexpr int TILE = THREADS * ITEMS;
   const int64_t tiles = (n + TILE - 1) / TILE;
   const size_t smem = static_cast<size_t>(TILE) * 8;
-  auto k = sort_pass_kernel<THREADS, ITEMS>;
-  if (!allow_smem(k, smem)) return CRYS_ECUDA;
+  using Kernel = void (*)(PassArgs);
+  const Kernel kernels[kPasses] = {sort_pass_kernel<THREADS, ITEMS, 0>, sort_pass_kernel<THREADS, ITEMS, 1>,
+                                   sort_pass_kernel<THREADS, ITEMS, 2>, sort_pass_kernel<THREADS, ITEMS, 3>};
+  for (int p = 0; p < kPasses; ++p)
+    if (!allow_smem(kernels[p], smem)) return CRYS_ECUDA;
   int32_t* tk = reinterpret_cast<int32_t*>(temp + L.tmp_keys);
   int32_t* tv = reinterpret_cast<int32_t*>(temp + L.tmp_vals);
   const int32_t* src_k[kPasses] = {keys_in, tk, keys_out, tk};
@@ -340,7 +355,7 @@ int run_passes(const int32_t* keys_in, const int32_t* vals_in, int32_t* keys_out
     a.tile_counter = reinterpret_cast<unsigned int*>(temp + L.counters) + p;
     if (cudaMemsetAsync(a.status, 0, static_cast<size_t>(tiles) * kRadix * 4, s) != cudaSuccess)
       return CRYS_ECUDA;
-    k<<<static_cast<unsigned int>(tiles), THREADS, smem, s>>>(a);
+    kernels[p]<<<static_cast<unsigned int>(tiles), THREADS, smem, s>>>(a);
     note_launch();
     if (check_launch() != CRYS_OK) return CRYS_ECUDA;
   }
