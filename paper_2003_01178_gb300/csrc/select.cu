@@ -17,6 +17,7 @@
 // ids handed out in order by an atomic counter, so a tile only waits on tiles that
 // running blocks already hold) and the result is in input order.
 #include <mutex>
+#include <type_traits>
 
 #include "common.cuh"
 #include "pipeline.cuh"
@@ -138,22 +139,30 @@ __global__ void __launch_bounds__(THREADS) select_kernel(SelectArgs a) {
     // bitmap in registers.
     int32_t v[ITEMS];
     uint32_t bits = 0;
+    // a full tile (all but possibly the last) reads the stage without tail checks
+    auto load_pred = [&](auto full_tag) {
+      constexpr bool FULL = decltype(full_tag)::value;
 #pragma unroll
-    for (int j = 0; j < VEC; ++j) {
-      const int p = warp * WROWS + j * 128 + lane * 4;
-      const int4 q = stage_read4(st, a.x + row0, p, bulk, valid);
-      v[4 * j + 0] = q.x;
-      v[4 * j + 1] = q.y;
-      v[4 * j + 2] = q.z;
-      v[4 * j + 3] = q.w;
+      for (int j = 0; j < VEC; ++j) {
+        const int p = warp * WROWS + j * 128 + lane * 4;
+        const int4 q = FULL ? *reinterpret_cast<const int4*>(st + p) : stage_read4(st, a.x + row0, p, bulk, valid);
+        v[4 * j + 0] = q.x;
+        v[4 * j + 1] = q.y;
+        v[4 * j + 2] = q.z;
+        v[4 * j + 3] = q.w;
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        // lo <= v <= hi as one unsigned comparison (span = hi - lo, lo <= hi)
-        const bool hit = (p + e < valid) &&
-                         static_cast<uint32_t>(v[4 * j + e]) - static_cast<uint32_t>(a.lo) <= a.span;
-        bits |= static_cast<uint32_t>(hit) << (4 * j + e);
+        for (int e = 0; e < 4; ++e) {
+          // lo <= v <= hi as one unsigned comparison (span = hi - lo, lo <= hi)
+          const bool hit = (FULL || p + e < valid) &&
+                           static_cast<uint32_t>(v[4 * j + e]) - static_cast<uint32_t>(a.lo) <= a.span;
+          bits |= static_cast<uint32_t>(hit) << (4 * j + e);
+        }
       }
-    }
+    };
+    if (valid == TILE)
+      load_pred(std::true_type{});
+    else
+      load_pred(std::false_type{});
     // BlockScan inside the warp: one scan of the per-lane counts of all VEC groups at
     // once (group j's count in byte j; a group's warp total is at most 128).
     uint32_t packed = 0;
