@@ -157,15 +157,27 @@ __global__ void __launch_bounds__(THREADS) probe_kernel(ProbeArgs a) {
     const int bulk = valid & ~3;
     int32_t key[ITEMS], pay[ITEMS];
     uint32_t live = 0;
+    if (valid == TILE) {  // a full tile: the stage holds every row
 #pragma unroll
-    for (int j = 0; j < VEC; ++j) {
-      const int p = (j * THREADS + tid) * 4;
-      const int4 qk = stage_read4(stk, cols[0] + row0, p, bulk, valid);
-      const int4 qp = stage_read4(stp, cols[1] + row0, p, bulk, valid);
-      key[4 * j + 0] = qk.x; key[4 * j + 1] = qk.y; key[4 * j + 2] = qk.z; key[4 * j + 3] = qk.w;
-      pay[4 * j + 0] = qp.x; pay[4 * j + 1] = qp.y; pay[4 * j + 2] = qp.z; pay[4 * j + 3] = qp.w;
+      for (int j = 0; j < VEC; ++j) {
+        const int p = (j * THREADS + tid) * 4;
+        const int4 qk = *reinterpret_cast<const int4*>(stk + p);
+        const int4 qp = *reinterpret_cast<const int4*>(stp + p);
+        key[4 * j + 0] = qk.x; key[4 * j + 1] = qk.y; key[4 * j + 2] = qk.z; key[4 * j + 3] = qk.w;
+        pay[4 * j + 0] = qp.x; pay[4 * j + 1] = qp.y; pay[4 * j + 2] = qp.z; pay[4 * j + 3] = qp.w;
+      }
+      live = ITEMS == 32 ? 0xFFFFFFFFu : ((1u << ITEMS) - 1u);
+    } else {
 #pragma unroll
-      for (int e = 0; e < 4; ++e) live |= static_cast<uint32_t>(p + e < valid) << (4 * j + e);
+      for (int j = 0; j < VEC; ++j) {
+        const int p = (j * THREADS + tid) * 4;
+        const int4 qk = stage_read4(stk, cols[0] + row0, p, bulk, valid);
+        const int4 qp = stage_read4(stp, cols[1] + row0, p, bulk, valid);
+        key[4 * j + 0] = qk.x; key[4 * j + 1] = qk.y; key[4 * j + 2] = qk.z; key[4 * j + 3] = qk.w;
+        pay[4 * j + 0] = qp.x; pay[4 * j + 1] = qp.y; pay[4 * j + 2] = qp.z; pay[4 * j + 3] = qp.w;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) live |= static_cast<uint32_t>(p + e < valid) << (4 * j + e);
+      }
     }
     // BlockLookup: all first-slot reads issued before any is examined.
     uint32_t h[ITEMS];
