@@ -184,6 +184,21 @@ __global__ void __launch_bounds__(THREADS) select_kernel(SelectArgs a) {
     }
     if (lane == 0) wtot[warp] = run;
     __syncthreads();  // every warp has read the stage and published its count
+    if (!ORDERED) {
+      // A tile without matches needs no reservation and no store: every thread sees the
+      // same warp totals, so the whole block skips the second barrier together.  (The
+      // totals are next written after the next iteration's stage barrier.)
+      int tile_total = 0;
+#pragma unroll
+      for (int w = 0; w < WARPS; ++w) tile_total += wtot[w];
+      if (tile_total == 0) {
+        if (tid == 0) {
+          fence_proxy_async_smem();
+          issue(s);
+        }
+        continue;
+      }
+    }
     if (warp == 0) {
       if (lane == 0) {  // the stage is free: refill it now, while the tile is written
         fence_proxy_async_smem();
