@@ -10,10 +10,16 @@
 //                       L2 a few tiles ahead (bulk prefetch), and the evaluation is
 //                       branch-light: every column the query reads is loaded for every
 //                       row and predicates only clear bits of a row bitmap.
+//                       With few tiles per block, all of a tile's loads are issued
+//                       before any value is used.
 //  * shared_scan_kernel up to 32 queries over the same fact table: each tile of the
 //                       union of their columns crosses HBM once, and each (foreign
 //                       key, table) pair that several queries join through is probed
-//                       once per row for all of them.
+//                       once per row for all of them.  Serves batches with joins on
+//                       tables that are not direct.
+//  * annotate_kernel, tagged_scan_kernel (and the graph-replayable prepare_kernel,
+//                       tagged_scan_kernel_dev) the shared scan over direct dimension
+//                       tables with per-batch query bitmaps (see below).
 #include "common.cuh"
 #include "pipeline.cuh"
 #include "tiles.h"

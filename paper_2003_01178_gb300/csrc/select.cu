@@ -7,10 +7,12 @@
 // run) -> BlockStore (coalesced stores of each warp's run).
 //
 // Each warp owns a contiguous run of ITEMS*32 rows of the tile (lane l reads the
-// 4-value groups j*128 + 4l, j < ITEMS/4), compacts its selected values in input order
-// into its own shared-memory run, and after one block barrier (warp totals -> offsets
-// and the tile's single output reservation) stores that run with coalesced writes; the
-// stage is handed back to the copy engine right after the first barrier.
+// 4-value groups j*128 + 4l, j < ITEMS/4) and compacts its selected values in input
+// order into its own shared-memory run.  A first block barrier publishes the warp totals
+// (the stage goes back to the copy engine right after it); warp 0 turns them into
+// offsets and makes the tile's single output reservation; after a second barrier every
+// warp stores its run with coalesced writes.  In the unordered mode a tile without
+// matches stops after the first barrier.  Full tiles read the stage without tail checks.
 //
 // Output reservation: mode 0 adds the tile's count to the global cursor with one
 // atomic (the paper's scheme); mode 1 chains tiles with a decoupled look-back (tile
