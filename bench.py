@@ -2,14 +2,16 @@
 
 Default workload (``--workload served``): the served star-schema stream — a fact table of
 600M rows x 8 int32 columns resident in HBM and four dimensions (2556 / 200K / 3M / 1.4M
-rows); a step is one batch of 32 seeded select-join-group-by queries: their dimension
-hash tables are built (one build kernel per join) and all 32 run in ONE shared scan of
-the fact table.  ``value`` is queries/s over the K timed steps (CUDA events, inputs
-resident, fact table 19.2 GB >> L2).  The JSON line also carries the one-query-at-a-time
-baseline on the same GPU, the served loop (continuous batching through the public API:
-queries in from the host, results back to pinned host memory) with p50/p99 latency, the
-dominant kernel's roofline, the CPU oracle timed on a sample of the same workload, SM
-clocks sampled during the timed region, and the number of library kernels launched.
+rows) held as direct tables of packed attribute codes; a step is one batch of 32 seeded
+select-join-group-by queries compiled against those tables and run in ONE tagged shared
+scan of the fact table (the batch's dimension rows tagged with query bitmaps, then one
+scan).  ``value`` is queries/s over the K timed steps (CUDA events, inputs resident, fact
+table 19.2 GB >> L2).  The JSON line also carries the one-query-at-a-time baseline on the
+same GPU, the serving loop (continuous batching over row segments through the public
+API, every launch a CUDA-graph replay: queries in from the host, results back to pinned
+host memory) with p50/p99 latency at several offered loads, the dominant kernel's
+roofline, the CPU oracle timed on a sample of the same workload, SM clocks sampled
+during the timed region, and the number of library kernels launched.
 
 Other workloads (``--workload select|project|join|sort|q1``) time one operator of the
 hot path each and report GB/s of algorithmic traffic against measured HBM bandwidth.
