@@ -7,8 +7,9 @@ PyTorch supplies device memory and streams.  There is no CPU fallback: importing
 operators without the built library raises.
 
 Convenience wrappers (``select``, ``project``, ``HashTable``, ``probe_aggregate``,
-``sort``, ``run_plan``, ``run_plans``) allocate outputs and scratch with torch and call
-the ``crys_*`` functions.
+``sort``, ``make_table``, ``make_plan``, ``run_plan``) allocate outputs and scratch with
+torch and call the ``crys_*`` functions; ``starschema`` (resident star schema, tagged
+shared scans, graph-replayed launches) and ``server`` (continuous batching) build on them.
 """
 from __future__ import annotations
 
