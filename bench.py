@@ -276,11 +276,11 @@ def run_served(args, rank, world, local):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(elapsed_ms / args.steps, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
         "data": "synthetic (seeded counter-based generator, generated in HBM)",
-        "config": {"workload": "served star-schema stream: fact 600M rows x 8 int32 cols (19.2 GB), "
-                               "dims 2556/200K/3M/1.4M rows, batches of 32 seeded select-join-group-by "
-                               "queries (1-4 joins, selectivity 1e-4..0.5, <=1e4 groups, int64 sums)",
+        "config": {"workload": f"served star-schema stream: fact 600M rows x 8 int32 cols (19.2 GB), "
+                               f"dims 2556/200K/3M/1.4M rows, batches of {BATCH} seeded select-join-group-by "
+                               f"queries (1-4 joins, selectivity 1e-4..0.5, <=1e4 groups, int64 sums)",
                    "fact_rows": store.n_rows, "batch_queries": BATCH,
-                   "step": "compile 32 queries against the resident direct dimension tables + one tagged "
+                   "step": f"compile {BATCH} queries against the resident direct dimension tables + one tagged "
                            "shared scan of the fact table: annotate_kernel tags every dimension row with "
                            "the bitmap of the batch's queries it satisfies, tagged_scan_kernel reads one "
                            "tag per dimension and fact row and finishes only the qualifying (row, query) "
@@ -726,6 +726,7 @@ def run_reference(args, rank, world):
 # ----------------------------------------------------------------------------- main
 
 def main():
+    global BATCH
     p = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     p.add_argument("--gpus", type=int, default=1)
     p.add_argument("--steps", type=int, default=10)
@@ -736,6 +737,7 @@ def main():
     p.add_argument("--dim-scale", type=float, default=1.0)
     p.add_argument("--seed", type=int, default=0xC0FFEE + 4)
     p.add_argument("--segments", type=int, default=8)
+    p.add_argument("--batch", type=int, default=BATCH, help="queries per shared scan (1..32)")
     p.add_argument("--served-queries", type=int, default=512)
     p.add_argument("--cpu-sample-rows", type=int, default=2_000_000)
     p.add_argument("--cpu-queries", type=int, default=4, help="queries per step timed on the CPU")
@@ -746,6 +748,9 @@ def main():
     args = p.parse_args()
     if args.warmup < 3:
         raise SystemExit("at least 3 warm-up steps")
+    if not 1 <= args.batch <= 32:
+        raise SystemExit("--batch must be in 1..32")
+    BATCH = args.batch
     if args.workload == "served" and args.rows is None:
         args.rows = 600_000_000
     rank, world, local = dist_setup(args)
