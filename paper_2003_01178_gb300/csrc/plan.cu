@@ -757,11 +757,19 @@ __global__ void __launch_bounds__(THREADS, (24 * kWarp) / THREADS > 0 ? (24 * kW
 // verdict at once: the AND of the entries' bitmaps.  Only the (row, query) pairs left
 // set are expanded, compacted per warp and finished one pair per lane (fact predicates,
 // group code, aggregate), so a query costs in proportion to the rows it keeps.
+//
+// Finishing reads, per pair, the pairs' values of its row and the fact columns of its
+// query's predicates and aggregate.  Both are put in shared memory by the warp that owns
+// the rows, during the lookups: one region of values per pair and one per fact column the
+// batch finishes with ("staged" columns), all with the same item-major layout (value of
+// item i of thread t at i * THREADS + t).  The lanes of a round finish rows of different
+// threads of the warp, so distinct rows fall in distinct banks; regions are padded by 8
+// words so that one row's values in different regions do too.
 
 constexpr int kMaxTagPairs = 8;
 constexpr int kMaxTagEntries = CRYS_MAX_PLANS * CRYS_MAX_JOINS;
 // A query's descriptor in shared memory: 16-byte groups of fields read with vector
-// loads.  Lanes finishing pairs of different queries read the same group of different
+// loads; a column field holds the index of the column's value region.  Lanes finishing pairs of different queries read the same group of different
 // descriptors; a stride of 17 groups puts 8 such lanes in 8 different bank quadruples.
 // Unused predicates and groups hold entries that always pass, so every lane runs the
 // same instructions whatever query it finishes.
@@ -847,6 +855,8 @@ struct TagHead {
   int32_t smem_bytes;  // dynamic shared memory the launch provides
   int32_t* err;
   TagScanPair pairs[kMaxTagPairs];
+  int32_t n_stage;                    // fact columns staged for finishing
+  int32_t stage_col[CRYS_MAX_COLS];   // staged column s -> fact column (region n_pairs + s)
 };
 
 struct TagArgs : TagHead {
@@ -856,20 +866,22 @@ struct TagArgs : TagHead {
 __device__ __forceinline__ int4 lds4(const int32_t* p) { return *reinterpret_cast<const int4*>(p); }
 
 // Finishes one (row, query) pair whose dimension verdicts all passed: fact predicates,
-// group code from the pairs' values, aggregate, accumulation.
-template <int TILE>
-__device__ __forceinline__ void finish_pair(const int32_t* D, const int32_t* const* cols, int64_t grow, int r,
-                                            const int32_t* pv, const SharedAcc& acc, int32_t* err) {
+// group code from the pairs' values, aggregate, accumulation.  `vals` holds the value
+// regions (pairs, then staged columns; PVS words apart) and `t` is the row's item-major
+// index in them.
+template <int PVS>
+__device__ __forceinline__ void finish_pair(const int32_t* D, const int32_t* vals, int t, const SharedAcc& acc,
+                                            int32_t* err) {
   const int4 g0 = lds4(D), g1 = lds4(D + 4), g2 = lds4(D + 8), g3 = lds4(D + 12);
-  // every column load in flight together: aggregate operands and two predicates
-  const int32_t xa = ld_cached(cols[g0.x] + grow);
-  const int32_t xb = ld_cached(cols[g0.y] + grow);
-  const int32_t x0 = ld_cached(cols[g1.x] + grow);
-  const int32_t x1 = ld_cached(cols[g1.w] + grow);
+  const int32_t* row = vals + t;
+  const int32_t xa = row[g0.x * PVS];
+  const int32_t xb = row[g0.y * PVS];
+  const int32_t x0 = row[g1.x * PVS];
+  const int32_t x1 = row[g1.w * PVS];
   bool ok = in_span(x0, g1.y, static_cast<uint32_t>(g1.z)) & in_span(x1, g2.x, static_cast<uint32_t>(g2.y));
   for (int f = 2; f < g2.z; ++f) {
     const int32_t* P = D + kDMorePreds + 3 * (f - 2);
-    ok = ok && in_span(ld_cached(cols[P[0]] + grow), P[1], static_cast<uint32_t>(P[2]));
+    ok = ok && in_span(row[P[0] * PVS], P[1], static_cast<uint32_t>(P[2]));
   }
   if (!ok) return;
   int32_t gid = 0;
@@ -877,13 +889,13 @@ __device__ __forceinline__ void finish_pair(const int32_t* D, const int32_t* con
 #pragma unroll
   for (int g = 0; g < 2; ++g) {
     const int4 G = lds4(D + kDGroup0 + 4 * g);
-    const uint32_t code = (static_cast<uint32_t>(pv[(G.x >> 8) * TILE + r]) >> (G.x & 31)) & static_cast<uint32_t>(G.y);
+    const uint32_t code = (static_cast<uint32_t>(row[(G.x >> 8) * PVS]) >> (G.x & 31)) & static_cast<uint32_t>(G.y);
     bad |= static_cast<uint32_t>(code >= static_cast<uint32_t>(G.z));
     gid += static_cast<int32_t>(code) * G.w;
   }
   for (int g = 2; g < g2.w; ++g) {
     const int4 G = lds4(D + kDGroup0 + 4 * g);
-    const uint32_t code = (static_cast<uint32_t>(pv[(G.x >> 8) * TILE + r]) >> (G.x & 31)) & static_cast<uint32_t>(G.y);
+    const uint32_t code = (static_cast<uint32_t>(row[(G.x >> 8) * PVS]) >> (G.x & 31)) & static_cast<uint32_t>(G.y);
     bad |= static_cast<uint32_t>(code >= static_cast<uint32_t>(G.z));
     gid += static_cast<int32_t>(code) * G.w;
   }
@@ -910,18 +922,18 @@ __device__ __forceinline__ void finish_pair(const int32_t* D, const int32_t* con
   }
 }
 
-// Shared memory of a block: query descriptors, the fact column pointers, the pairs'
-// values of the tile's rows (pv[p * TILE + r]), one (row, query) list per warp, then the
-// group accumulators.
+// Shared memory of a block: query descriptors, the value regions of the tile's rows
+// (n_vals = pairs + staged columns, PVS words each), one (row, query) list per warp, then
+// the group accumulators.
 template <int THREADS, int ITEMS>
 struct TagSmem {
   static constexpr int TILE = THREADS * ITEMS;
-  static constexpr int LIST = 256;  // list window of a warp (a round averages a few per lane)
+  static constexpr int PVS = TILE + 8;  // region stride in words
+  static constexpr int LIST = 256;      // list window of a warp (a round averages a few per lane)
   static constexpr size_t desc_bytes = CRYS_MAX_PLANS * kDescWords * 4;
-  static constexpr size_t cols_off = (desc_bytes + 15) / 16 * 16;
-  static constexpr size_t pv_off = cols_off + CRYS_MAX_COLS * 8;
-  __host__ __device__ static size_t list_off(int n_pairs) { return pv_off + static_cast<size_t>(n_pairs) * TILE * 4; }
-  __host__ __device__ static size_t acc_off(int n_pairs) { return list_off(n_pairs) + static_cast<size_t>(THREADS / kWarp) * LIST * 2; }
+  static constexpr size_t vals_off = (desc_bytes + 15) / 16 * 16;
+  __host__ __device__ static size_t list_off(int n_vals) { return vals_off + static_cast<size_t>(n_vals) * PVS * 4; }
+  __host__ __device__ static size_t acc_off(int n_vals) { return list_off(n_vals) + static_cast<size_t>(THREADS / kWarp) * LIST * 2; }
 };
 
 template <int THREADS, int ITEMS>
@@ -930,24 +942,24 @@ __device__ __forceinline__ void tagged_scan_body(const TagHead& a, const int32_t
   constexpr int TILE = L::TILE;
   constexpr int VEC = ITEMS / 4;
   static_assert(TILE <= 2048, "a list entry holds an 11-bit tile row");
+  constexpr int PVS = L::PVS;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int tid = threadIdx.x, lane = tid % kWarp, warp = tid / kWarp;
+  const int n_vals = a.n_pairs + a.n_stage;
   int32_t* desc = reinterpret_cast<int32_t*>(smem_raw);
-  const int32_t** scols = reinterpret_cast<const int32_t**>(smem_raw + L::cols_off);
-  int32_t* pv = reinterpret_cast<int32_t*>(smem_raw + L::pv_off);
-  uint16_t* list = reinterpret_cast<uint16_t*>(smem_raw + L::list_off(a.n_pairs)) + warp * L::LIST;
+  int32_t* vals = reinterpret_cast<int32_t*>(smem_raw + L::vals_off);
+  uint16_t* list = reinterpret_cast<uint16_t*>(smem_raw + L::list_off(n_vals)) + warp * L::LIST;
   // arguments prepared for another tile shape, or accumulators past the shared memory
   // this launch has: refuse the work (uniformly in every block) instead of overrunning
   uint32_t dyn_smem;
   asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn_smem));
-  if (a.tile_shape != ((THREADS << 16) | ITEMS) ||
-      L::acc_off(a.n_pairs) + static_cast<size_t>(a.shared_groups) * 12 > dyn_smem) {
+  if (a.tile_shape != ((THREADS << 16) | ITEMS) || a.n_stage < 1 || a.n_stage > CRYS_MAX_COLS ||
+      L::acc_off(n_vals) + static_cast<size_t>(a.shared_groups) * 12 > dyn_smem) {
     if (tid == 0) set_error(a.err, CRYS_DEV_BOUNDS);
     return;
   }
-  const SharedAcc acc = shared_acc(smem_raw + L::acc_off(a.n_pairs), a.shared_groups);
+  const SharedAcc acc = shared_acc(smem_raw + L::acc_off(n_vals), a.shared_groups);
   for (int w = tid; w < a.n_queries * kDescWords; w += THREADS) desc[w] = desc_src[w];
-  if (tid < CRYS_MAX_COLS) scols[tid] = a.cols[tid];
   for (int g = tid; g < a.shared_groups; g += THREADS) {
     acc.sums[g] = 0;
     acc.counts[g] = 0;
@@ -990,13 +1002,22 @@ __device__ __forceinline__ void tagged_scan_body(const TagHead& a, const int32_t
         e[i] = (rm[i] && static_cast<uint32_t>(key[i]) < P.limit) ? ld_slot(P.ann + key[i], pol_table)
                                                                   : static_cast<uint64_t>(P.nonjoin);
 #pragma unroll
-      for (int j = 0; j < VEC; ++j) {
-#pragma unroll
-        for (int k = 0; k < 4; ++k) rm[4 * j + k] &= static_cast<uint32_t>(e[4 * j + k]);
-        *reinterpret_cast<int4*>(pv + p * TILE + (j * THREADS + tid) * 4) =
-            make_int4(static_cast<int32_t>(e[4 * j] >> 32), static_cast<int32_t>(e[4 * j + 1] >> 32),
-                      static_cast<int32_t>(e[4 * j + 2] >> 32), static_cast<int32_t>(e[4 * j + 3] >> 32));
+      for (int i = 0; i < ITEMS; ++i) {
+        rm[i] &= static_cast<uint32_t>(e[i]);
+        vals[p * PVS + i * THREADS + tid] = static_cast<int32_t>(e[i] >> 32);
       }
+    }
+    uint32_t any = 0;
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) any |= rm[i];
+    if (!__any_sync(0xFFFFFFFFu, any != 0)) continue;  // no pair of the warp's rows survives
+    // the fact columns the batch finishes with, beside the pairs' values
+    for (int c = 0; c < a.n_stage; ++c) {
+      int32_t x[ITEMS];
+#pragma unroll
+      for (int j = 0; j < VEC; ++j) unpack4(fk_cols.load4(a.stage_col[c], (j * THREADS + tid) * 4), x + 4 * j);
+#pragma unroll
+      for (int i = 0; i < ITEMS; ++i) vals[(a.n_pairs + c) * PVS + i * THREADS + tid] = x[i];
     }
     __syncwarp();  // values of the warp's rows visible to all its lanes
     // per item slot: expand each lane's (row, query) pairs into the warp's list, finish them
@@ -1006,7 +1027,7 @@ __device__ __forceinline__ void tagged_scan_body(const TagHead& a, const int32_t
       const int incl = warp_inclusive_scan(n, lane);
       const int total = __shfl_sync(0xFFFFFFFFu, incl, kWarp - 1);
       if (total == 0) continue;
-      const int r = ((i >> 2) * THREADS + tid) * 4 + (i & 3);
+      const int r = i * THREADS + tid;  // item-major index of the lane's row
       // the pairs go through the list in windows of L::LIST entries (one window unless
       // the round expands more pairs than that)
       for (int w0 = 0; w0 < total; w0 += L::LIST) {
@@ -1019,8 +1040,7 @@ __device__ __forceinline__ void tagged_scan_body(const TagHead& a, const int32_t
         for (int base = 0; base < wn; base += kWarp) {
           if (base + lane < wn) {
             const uint32_t ent = list[base + lane];
-            const int rr = static_cast<int>(ent & 0x7FFu);
-            finish_pair<TILE>(desc + (ent >> 11) * kDescWords, scols, row0 + rr, rr, pv, acc, a.err);
+            finish_pair<PVS>(desc + (ent >> 11) * kDescWords, vals, static_cast<int>(ent & 0x7FFu), acc, a.err);
           }
         }
         __syncwarp();  // the list is reused by the next window or item slot
@@ -1442,6 +1462,20 @@ bool tag_batch(const crys_plan* plans, const DevQuery* q, int n, TagBatch* tb) {
     tb->bytes += (static_cast<int64_t>(P.limit) * 8 + 15) / 16 * 16;
     if (P.limit > tb->max_slots) tb->max_slots = P.limit;
   }
+  // fact columns the batch finishes with: staged in value regions after the pairs'
+  int region_of[CRYS_MAX_COLS];
+  for (int c = 0; c < CRYS_MAX_COLS; ++c) {
+    region_of[c] = -1;
+    S.stage_col[c] = 0;
+  }
+  S.n_stage = 0;
+  auto region = [&](int32_t c) {
+    if (region_of[c] < 0) {
+      region_of[c] = A.n_pairs + S.n_stage;
+      S.stage_col[S.n_stage++] = c;
+    }
+    return region_of[c];
+  };
   // descriptors
   S.n_queries = n;
   S.all_mask = 0;
@@ -1456,14 +1490,14 @@ bool tag_batch(const crys_plan* plans, const DevQuery* q, int n, TagBatch* tb) {
     const int32_t pc[2] = {Q.n_preds > 0 ? Q.pred_col[0] : Q.agg_a, Q.n_preds > 1 ? Q.pred_col[1] : Q.agg_a};
     const int32_t pl[2] = {Q.n_preds > 0 ? Q.pred_lo[0] : 0, Q.n_preds > 1 ? Q.pred_lo[1] : 0};
     const uint32_t ps[2] = {Q.n_preds > 0 ? Q.pred_span[0] : 0xFFFFFFFFu, Q.n_preds > 1 ? Q.pred_span[1] : 0xFFFFFFFFu};
-    D[kDP0Col] = pc[0];
+    D[kDP0Col] = region(pc[0]);
     D[kDP0Lo] = pl[0];
     D[kDP0Span] = static_cast<int32_t>(ps[0]);
-    D[kDP1Col] = pc[1];
+    D[kDP1Col] = region(pc[1]);
     D[kDP1Lo] = pl[1];
     D[kDP1Span] = static_cast<int32_t>(ps[1]);
     for (int f = 2; f < Q.n_preds; ++f) {
-      D[kDMorePreds + 3 * (f - 2)] = Q.pred_col[f];
+      D[kDMorePreds + 3 * (f - 2)] = region(Q.pred_col[f]);
       D[kDMorePreds + 3 * (f - 2) + 1] = Q.pred_lo[f];
       D[kDMorePreds + 3 * (f - 2) + 2] = static_cast<int32_t>(Q.pred_span[f]);
     }
@@ -1486,8 +1520,8 @@ bool tag_batch(const crys_plan* plans, const DevQuery* q, int n, TagBatch* tb) {
     }
     D[kDGroups] = ng;
     // aggregate: a*b, or ca*a + cb*b (a: ca 1 cb 0 with b = a; a-b: 1, -1; a+b: 1, 1)
-    D[kDAggA] = Q.agg_a;
-    D[kDAggB] = Q.agg_op == CRYS_AGG_A ? Q.agg_a : Q.agg_b;
+    D[kDAggA] = region(Q.agg_a);
+    D[kDAggB] = region(Q.agg_op == CRYS_AGG_A ? Q.agg_a : Q.agg_b);
     D[kDMulAB] = Q.agg_op == CRYS_AGG_A_MUL_B ? 1 : 0;
     D[kDCoefA] = Q.agg_op == CRYS_AGG_A_MUL_B ? 0 : 1;
     D[kDCoefB] = Q.agg_op == CRYS_AGG_A_SUB_B ? -1 : (Q.agg_op == CRYS_AGG_A_ADD_B ? 1 : 0);
@@ -1558,7 +1592,7 @@ int launch_tagged(TagBatch& tb, const DevQuery* q, unsigned char* scratch, cudaS
     const int rc = check_launch();
     if (rc != CRYS_OK) return rc;
   }
-  const size_t fixed = L::acc_off(S.n_pairs);
+  const size_t fixed = L::acc_off(S.n_pairs + S.n_stage);
   const int64_t used = assign_accumulators(S, q, kTagShare > fixed ? kTagShare - fixed : 0);
   S.tile_shape = (THREADS << 16) | ITEMS;
   S.smem_bytes = static_cast<int32_t>(fixed + static_cast<size_t>(used) * 12);
@@ -1587,7 +1621,7 @@ int prepare_block(TagBatch& tb, const DevQuery* q, unsigned char* scratch, TagLa
   using L = TagSmem<THREADS, ITEMS>;
   place_annotations(tb, scratch);
   TagArgs& S = tb.scan;
-  const size_t fixed = L::acc_off(S.n_pairs);
+  const size_t fixed = L::acc_off(S.n_pairs + S.n_stage);
   if (fixed > kTagShare) return CRYS_EINVAL;
   assign_accumulators(S, q, kTagShare - fixed);
   S.tile_shape = (THREADS << 16) | ITEMS;
