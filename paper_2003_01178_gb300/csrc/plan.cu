@@ -474,6 +474,20 @@ struct SharedAcc {
   unsigned int* counts;
 };
 
+// 64-bit add to a shared-memory accumulator made of 32-bit atomics (the low word comes
+// first: the GPU is little-endian).  The add to the low word returns its previous value,
+// which tells whether it carried; the high word then receives the value's high half plus
+// that carry (skipped when both are zero).  Every carry is counted by the add that made
+// it, so the two words hold the exact sum modulo 2^64 once all adds are done.  On sm_103a
+// this measured faster than the 64-bit shared-memory atomic.
+__device__ __forceinline__ void shared_add_u64(unsigned long long* p, unsigned long long v) {
+  const uint32_t lo = static_cast<uint32_t>(v), hi = static_cast<uint32_t>(v >> 32);
+  uint32_t* w = reinterpret_cast<uint32_t*>(p);
+  const uint32_t old = atomicAdd(w, lo);
+  const uint32_t up = hi + (old + lo < old ? 1u : 0u);
+  if (up) atomicAdd(w + 1, up);
+}
+
 __device__ __forceinline__ SharedAcc shared_acc(unsigned char* base, int groups) {
   SharedAcc s;
   s.sums = reinterpret_cast<unsigned long long*>(base);
@@ -566,7 +580,7 @@ __global__ void __launch_bounds__(THREADS) plan_kernel(const __grid_constant__ P
     for (int i = 0; i < ITEMS; ++i) {
       if (!((alive >> i) & 1u)) continue;
       if (q.acc_mode == kAccShared) {
-        atomicAdd(acc.sums + gid[i], static_cast<unsigned long long>(val[i]));
+        shared_add_u64(acc.sums + gid[i], static_cast<unsigned long long>(val[i]));
         atomicAdd(acc.counts + gid[i], 1u);
       } else {
         red_add_global(q.sums + gid[i], static_cast<unsigned long long>(val[i]), pol_table);
@@ -720,7 +734,7 @@ __global__ void __launch_bounds__(THREADS, (24 * kWarp) / THREADS > 0 ? (24 * kW
         s_sum = warp_sum_u64(s_sum);
         s_cnt = warp_sum_u64(s_cnt);
         if (lane == 0 && s_cnt) {
-          atomicAdd(acc.sums + q.acc_off, static_cast<unsigned long long>(s_sum));
+          shared_add_u64(acc.sums + q.acc_off, static_cast<unsigned long long>(s_sum));
           atomicAdd(acc.counts + q.acc_off, static_cast<unsigned int>(s_cnt));
         }
       } else if (alive) {
@@ -728,7 +742,7 @@ __global__ void __launch_bounds__(THREADS, (24 * kWarp) / THREADS > 0 ? (24 * kW
         for (int i = 0; i < ITEMS; ++i) {
           if (!((alive >> i) & 1u)) continue;
           if (q.acc_mode == kAccShared) {
-            atomicAdd(acc.sums + q.acc_off + gid[i], static_cast<unsigned long long>(val[i]));
+            shared_add_u64(acc.sums + q.acc_off + gid[i], static_cast<unsigned long long>(val[i]));
             atomicAdd(acc.counts + q.acc_off + gid[i], 1u);
           } else {
             red_add_global(q.sums + gid[i], static_cast<unsigned long long>(val[i]), pol_table);
@@ -839,7 +853,23 @@ struct TagScanPair {
   uint32_t limit;
   int32_t fk_col;
   uint32_t nonjoin;
+  int32_t in_l1;  // entries small enough to stay in L1 (read with L1 allocation)
 };
+
+// Entries of a table up to this size are read through L1, where every tile's lookups
+// find them; the others bypass L1 so that they do not evict the small ones.
+constexpr int64_t kTagL1Bytes = 24 * 1024;
+
+__device__ __forceinline__ uint64_t ld_tag_l1(const uint64_t* p, uint64_t pol) {
+  uint64_t v;
+  asm volatile("ld.global.nc.L1::evict_last.L2::cache_hint.u64 %0, [%1], %2;" : "=l"(v) : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ uint64_t ld_tag_bypass(const uint64_t* p, uint64_t pol) {
+  uint64_t v;
+  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.u64 %0, [%1], %2;" : "=l"(v) : "l"(p), "l"(pol));
+  return v;
+}
 
 // Everything a tagged scan launch needs except the query descriptors (TagHead), and the
 // descriptors after it (TagArgs).
@@ -908,7 +938,7 @@ __device__ __forceinline__ void finish_pair(const int32_t* D, const int32_t* val
   const int64_t val = g3.x ? prod : lin;
   if (g0.z != kAccGlobal) {
     const int slot = g0.w + gid;
-    atomicAdd(acc.sums + slot, static_cast<unsigned long long>(val));
+    shared_add_u64(acc.sums + slot, static_cast<unsigned long long>(val));
     atomicAdd(acc.counts + slot, 1u);
   } else {
     const int4 ptrs = lds4(D + kDSums);
@@ -997,10 +1027,17 @@ __device__ __forceinline__ void tagged_scan_body(const TagHead& a, const int32_t
 #pragma unroll
       for (int j = 0; j < VEC; ++j) unpack4(fk_cols.load4(P.fk_col, (j * THREADS + tid) * 4), key + 4 * j);
       uint64_t e[ITEMS];
+      if (P.in_l1) {
 #pragma unroll
-      for (int i = 0; i < ITEMS; ++i)
-        e[i] = (rm[i] && static_cast<uint32_t>(key[i]) < P.limit) ? ld_slot(P.ann + key[i], pol_table)
-                                                                  : static_cast<uint64_t>(P.nonjoin);
+        for (int i = 0; i < ITEMS; ++i)
+          e[i] = (rm[i] && static_cast<uint32_t>(key[i]) < P.limit) ? ld_tag_l1(P.ann + key[i], pol_table)
+                                                                    : static_cast<uint64_t>(P.nonjoin);
+      } else {
+#pragma unroll
+        for (int i = 0; i < ITEMS; ++i)
+          e[i] = (rm[i] && static_cast<uint32_t>(key[i]) < P.limit) ? ld_tag_bypass(P.ann + key[i], pol_table)
+                                                                    : static_cast<uint64_t>(P.nonjoin);
+      }
 #pragma unroll
       for (int i = 0; i < ITEMS; ++i) {
         rm[i] &= static_cast<uint32_t>(e[i]);
@@ -1459,6 +1496,7 @@ bool tag_batch(const crys_plan* plans, const DevQuery* q, int n, TagBatch* tb) {
     S.pairs[p].limit = P.limit;
     S.pairs[p].fk_col = P.fk_col;
     S.pairs[p].nonjoin = P.nonjoin;
+    S.pairs[p].in_l1 = static_cast<int64_t>(P.limit) * 8 <= kTagL1Bytes ? 1 : 0;
     tb->bytes += (static_cast<int64_t>(P.limit) * 8 + 15) / 16 * 16;
     if (P.limit > tb->max_slots) tb->max_slots = P.limit;
   }
