@@ -782,12 +782,13 @@ __global__ void __launch_bounds__(THREADS, (24 * kWarp) / THREADS > 0 ? (24 * kW
 
 constexpr int kMaxTagPairs = 8;
 constexpr int kMaxTagEntries = CRYS_MAX_PLANS * CRYS_MAX_JOINS;
-// A query's descriptor in shared memory: 16-byte groups of fields read with vector
-// loads; a column field holds the index of the column's value region.  Lanes finishing pairs of different queries read the same group of different
-// descriptors; a stride of 17 groups puts 8 such lanes in 8 different bank quadruples.
-// Unused predicates and groups hold entries that always pass, so every lane runs the
-// same instructions whatever query it finishes.
-constexpr int kDescWords = 68;
+// A query's descriptor: kDescWords 32-bit fields (a column field holds the index of the
+// column's value region), stored field-major in shared memory: field f of query q at
+// f * CRYS_MAX_PLANS + q.  The lanes of a finishing round read the same field of the
+// queries they finish, so distinct queries fall in distinct banks and equal ones share a
+// broadcast: one wavefront per field read.  Unused predicates and groups hold entries
+// that always pass, so every lane runs the same instructions whatever query it finishes.
+constexpr int kDescWords = 54;
 enum DescField : int {
   kDAggA = 0, kDAggB = 1, kDAccMode = 2, kDAccOff = 3,       // group 0
   kDP0Col = 4, kDP0Lo = 5, kDP0Span = 6, kDP1Col = 7,        // group 1: fact predicates 0, 1
@@ -797,6 +798,14 @@ enum DescField : int {
   kDSums = 32,        // 2 words, then counts (2 words)
   kDCounts = 34,
   kDMorePreds = 36,   // predicates 2..7: column, lo, span
+};
+static_assert(kDMorePreds + 3 * (CRYS_MAX_PREDS - 2) <= kDescWords, "descriptor fields");
+
+// Field access to one query's descriptor in the field-major layout.
+template <typename T>
+struct DescView {
+  T* base;  // field 0 of the query
+  __host__ __device__ __forceinline__ T& operator[](int f) const { return base[f * CRYS_MAX_PLANS]; }
 };
 
 struct TagPair {
@@ -893,59 +902,55 @@ struct TagArgs : TagHead {
   int32_t desc[CRYS_MAX_PLANS * kDescWords];
 };
 
-__device__ __forceinline__ int4 lds4(const int32_t* p) { return *reinterpret_cast<const int4*>(p); }
-
 // Finishes one (row, query) pair whose dimension verdicts all passed: fact predicates,
 // group code from the pairs' values, aggregate, accumulation.  `vals` holds the value
 // regions (pairs, then staged columns; PVS words apart) and `t` is the row's item-major
 // index in them.
 template <int PVS>
-__device__ __forceinline__ void finish_pair(const int32_t* D, const int32_t* vals, int t, const SharedAcc& acc,
-                                            int32_t* err) {
-  const int4 g0 = lds4(D), g1 = lds4(D + 4), g2 = lds4(D + 8), g3 = lds4(D + 12);
+__device__ __forceinline__ void finish_pair(const DescView<const int32_t> D, const int32_t* vals, int t,
+                                            const SharedAcc& acc, int32_t* err) {
   const int32_t* row = vals + t;
-  const int32_t xa = row[g0.x * PVS];
-  const int32_t xb = row[g0.y * PVS];
-  const int32_t x0 = row[g1.x * PVS];
-  const int32_t x1 = row[g1.w * PVS];
-  bool ok = in_span(x0, g1.y, static_cast<uint32_t>(g1.z)) & in_span(x1, g2.x, static_cast<uint32_t>(g2.y));
-  for (int f = 2; f < g2.z; ++f) {
-    const int32_t* P = D + kDMorePreds + 3 * (f - 2);
-    ok = ok && in_span(row[P[0] * PVS], P[1], static_cast<uint32_t>(P[2]));
+  const int32_t xa = row[D[kDAggA] * PVS];
+  const int32_t xb = row[D[kDAggB] * PVS];
+  const int32_t x0 = row[D[kDP0Col] * PVS];
+  const int32_t x1 = row[D[kDP1Col] * PVS];
+  bool ok = in_span(x0, D[kDP0Lo], static_cast<uint32_t>(D[kDP0Span])) &
+            in_span(x1, D[kDP1Lo], static_cast<uint32_t>(D[kDP1Span]));
+  const int n_preds = D[kDPreds];
+  for (int f = 2; f < n_preds; ++f) {
+    const int b = kDMorePreds + 3 * (f - 2);
+    ok = ok && in_span(row[D[b] * PVS], D[b + 1], static_cast<uint32_t>(D[b + 2]));
   }
   if (!ok) return;
   int32_t gid = 0;
   uint32_t bad = 0;
-#pragma unroll
-  for (int g = 0; g < 2; ++g) {
-    const int4 G = lds4(D + kDGroup0 + 4 * g);
-    const uint32_t code = (static_cast<uint32_t>(row[(G.x >> 8) * PVS]) >> (G.x & 31)) & static_cast<uint32_t>(G.y);
-    bad |= static_cast<uint32_t>(code >= static_cast<uint32_t>(G.z));
-    gid += static_cast<int32_t>(code) * G.w;
-  }
-  for (int g = 2; g < g2.w; ++g) {
-    const int4 G = lds4(D + kDGroup0 + 4 * g);
-    const uint32_t code = (static_cast<uint32_t>(row[(G.x >> 8) * PVS]) >> (G.x & 31)) & static_cast<uint32_t>(G.y);
-    bad |= static_cast<uint32_t>(code >= static_cast<uint32_t>(G.z));
-    gid += static_cast<int32_t>(code) * G.w;
-  }
+  auto group = [&](int g) {
+    const int32_t gx = D[kDGroup0 + 4 * g];
+    const uint32_t code = (static_cast<uint32_t>(row[(gx >> 8) * PVS]) >> (gx & 31)) &
+                          static_cast<uint32_t>(D[kDGroup0 + 4 * g + 1]);
+    bad |= static_cast<uint32_t>(code >= static_cast<uint32_t>(D[kDGroup0 + 4 * g + 2]));
+    gid += static_cast<int32_t>(code) * D[kDGroup0 + 4 * g + 3];
+  };
+  group(0);
+  group(1);
+  const int n_groups = D[kDGroups];
+  for (int g = 2; g < n_groups; ++g) group(g);
   if (bad) {
     set_error(err, CRYS_DEV_BAD_GROUP);
     return;
   }
   const int64_t prod = static_cast<int64_t>(xa) * xb;
-  const int64_t lin = static_cast<int64_t>(xa) * g3.y + static_cast<int64_t>(xb) * g3.z;
-  const int64_t val = g3.x ? prod : lin;
-  if (g0.z != kAccGlobal) {
-    const int slot = g0.w + gid;
+  const int64_t lin = static_cast<int64_t>(xa) * D[kDCoefA] + static_cast<int64_t>(xb) * D[kDCoefB];
+  const int64_t val = D[kDMulAB] ? prod : lin;
+  if (D[kDAccMode] != kAccGlobal) {
+    const int slot = D[kDAccOff] + gid;
     shared_add_u64(acc.sums + slot, static_cast<unsigned long long>(val));
     atomicAdd(acc.counts + slot, 1u);
   } else {
-    const int4 ptrs = lds4(D + kDSums);
     unsigned long long* sums = reinterpret_cast<unsigned long long*>(
-        (static_cast<uint64_t>(static_cast<uint32_t>(ptrs.y)) << 32) | static_cast<uint32_t>(ptrs.x));
+        (static_cast<uint64_t>(static_cast<uint32_t>(D[kDSums + 1])) << 32) | static_cast<uint32_t>(D[kDSums]));
     unsigned long long* counts = reinterpret_cast<unsigned long long*>(
-        (static_cast<uint64_t>(static_cast<uint32_t>(ptrs.w)) << 32) | static_cast<uint32_t>(ptrs.z));
+        (static_cast<uint64_t>(static_cast<uint32_t>(D[kDCounts + 1])) << 32) | static_cast<uint32_t>(D[kDCounts]));
     const uint64_t keep = policy_evict_last();
     red_add_global(sums + gid, static_cast<unsigned long long>(val), keep);
     if (counts) red_add_global(counts + gid, 1ull, keep);
@@ -989,7 +994,7 @@ __device__ __forceinline__ void tagged_scan_body(const TagHead& a, const int32_t
     return;
   }
   const SharedAcc acc = shared_acc(smem_raw + L::acc_off(n_vals), a.shared_groups);
-  for (int w = tid; w < a.n_queries * kDescWords; w += THREADS) desc[w] = desc_src[w];
+  for (int w = tid; w < CRYS_MAX_PLANS * kDescWords; w += THREADS) desc[w] = desc_src[w];
   for (int g = tid; g < a.shared_groups; g += THREADS) {
     acc.sums[g] = 0;
     acc.counts[g] = 0;
@@ -1077,7 +1082,8 @@ __device__ __forceinline__ void tagged_scan_body(const TagHead& a, const int32_t
         for (int base = 0; base < wn; base += kWarp) {
           if (base + lane < wn) {
             const uint32_t ent = list[base + lane];
-            finish_pair<PVS>(desc + (ent >> 11) * kDescWords, vals, static_cast<int>(ent & 0x7FFu), acc, a.err);
+            finish_pair<PVS>(DescView<const int32_t>{desc + (ent >> 11)}, vals, static_cast<int>(ent & 0x7FFu), acc,
+                             a.err);
           }
         }
         __syncwarp();  // the list is reused by the next window or item slot
@@ -1086,7 +1092,7 @@ __device__ __forceinline__ void tagged_scan_body(const TagHead& a, const int32_t
   }
   __syncthreads();
   for (int qi = 0; qi < a.n_queries; ++qi) {
-    const int32_t* D = desc + qi * kDescWords;
+    const DescView<const int32_t> D{desc + qi};
     if (D[kDAccMode] == kAccGlobal) continue;
     unsigned long long* sums = reinterpret_cast<unsigned long long*>(
         (static_cast<uint64_t>(static_cast<uint32_t>(D[kDSums + 1])) << 32) | static_cast<uint32_t>(D[kDSums]));
@@ -1520,7 +1526,7 @@ bool tag_batch(const crys_plan* plans, const DevQuery* q, int n, TagBatch* tb) {
   for (int w = 0; w < CRYS_MAX_PLANS * kDescWords; ++w) S.desc[w] = 0;
   for (int qi = 0; qi < n; ++qi) {
     const DevQuery& Q = q[qi];
-    int32_t* D = S.desc + qi * kDescWords;
+    const DescView<int32_t> D{S.desc + qi};
     if (!Q.never) S.all_mask |= 1u << qi;
     // fact predicates: the first two in fixed fields (an unused one always passes: any
     // value of the aggregate column lies in [0, 0 + 2^32 - 1]), the rest in a list
@@ -1598,7 +1604,7 @@ int64_t assign_accumulators(TagArgs& S, const DevQuery* q, size_t budget) {
   int64_t used = 0;
   for (int oi = 0; oi < S.n_queries; ++oi) {
     const int qi = order[oi];
-    int32_t* D = S.desc + qi * kDescWords;
+    const DescView<int32_t> D{S.desc + qi};
     if (static_cast<size_t>(used + q[qi].groups) * 12 <= budget) {
       D[kDAccMode] = kAccShared;
       D[kDAccOff] = static_cast<int32_t>(used);
