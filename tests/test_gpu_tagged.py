@@ -186,3 +186,32 @@ def test_tagged_every_row_expands_every_query(crys, orc, world):
     for (joins, preds, agg), (s, c) in zip(qs, outs):
         rs, rc = orc.run_plan_raw(world["fact"], preds, [o for _, o in joins], agg)
         assert np.array_equal(s.cpu().numpy(), rs) and np.array_equal(c.cpu().numpy(), rc)
+
+
+@pytest.mark.parametrize("variant", [0, 3])
+def test_tagged_every_fact_column_finishes(crys, orc, world, variant):
+    """Every fact column is read by some query's predicates or aggregate (foreign-key
+    columns included), through all four (column, table) pairs, with more than two fact
+    predicates: each column is staged beside the pairs' values and read back from there."""
+    crys.crys_set_tile(crys.OP_SHARED_SCAN, variant)
+    d0, d1, t0, t1 = world["d0"], world["d1"], world["t0"], world["t1"]
+
+    def j(fk, table, dim, field, card, name, fps=()):
+        return ((fk, table, card, field if card else (0, 0), [(*field, lo, hi) for lo, hi in fps]),
+                {"fk_col": fk, "keys": dim["key"], "preds": [(dim[name], lo, hi) for lo, hi in fps],
+                 "group": dim[name] if card else None, "card": card or 1})
+
+    qs = [
+        ([j(0, t0, d0, X, 16, "x")], [(1, 0, 40)], ("sum", 0, None)),
+        ([j(1, t0, d0, Y, 0, "y", [(0, 50)])], [(0, 0, 500), (3, 1, 9)], ("mul", 1, 3)),
+        ([j(1, t1, d1, Z, 8, "z")], [(2, 5, 45), (3, 0, 8), (4, 10, 99_000), (0, -3, 900)], ("sub", 4, 2)),
+        ([j(0, t1, d1, Z, 0, "z", [(1, 6)])], [], ("add", 0, 1)),
+        ([j(0, t0, d0, Y, 0, "y", [(20, 80)]), j(1, t1, d1, Z, 8, "z")], [(4, 1, 50_000)], ("add", 3, 4)),
+    ]
+    plans, outs = _plans(crys, qs)
+    assert _tagged(crys, world, plans) > 0
+    for (joins, preds, agg), (s, c) in zip(qs, outs):
+        rs, rc = orc.run_plan_raw(world["fact"], preds, [o for _, o in joins], agg)
+        assert np.array_equal(s.cpu().numpy(), rs) and np.array_equal(c.cpu().numpy(), rc)
+    crys.check_device_errors()
+    crys.crys_set_tile(crys.OP_SHARED_SCAN, 0)
