@@ -240,7 +240,7 @@ def run_served(args, rank, world, local):
         return qs, cqs
 
     tune_cqs = [store.compile(q, mode="resident") for q in batch_queries(seed, 20_000, rank)]
-    tile = autotune(crys.OP_SHARED_SCAN, lambda: store.run_shared(tune_cqs), args)
+    tile = autotune(crys.OP_TAGGED_SCAN, lambda: store.run_shared(tune_cqs), args)
     del tune_cqs
     for w in range(args.warmup):
         one_step(10_000 + w)

@@ -327,14 +327,18 @@ int crys_tagged_launch(const void* dev_block, crys_stream s);
 /* ------------------------------------------------------------------ tile shapes
  * Each operator is compiled for several tile shapes (threads per block x items per
  * thread, Section 3.3).  crys_tile_variants lists them; crys_set_tile picks the one
- * used by later calls in this process (an autotuner sweeps and persists the choice). */
+ * used by later calls in this process (an autotuner sweeps and persists the choice).
+ * CRYS_OP_SHARED_SCAN is crys_run_plans (also when crys_run_plans_tagged falls back to
+ * it); CRYS_OP_TAGGED_SCAN is the tagged scan of crys_run_plans_tagged and of the
+ * replayable launch (a block must be launched under the shape it was prepared for). */
 #define CRYS_OP_SELECT 0
 #define CRYS_OP_PROJECT 1
 #define CRYS_OP_PROBE 2
 #define CRYS_OP_PLAN 3
 #define CRYS_OP_SHARED_SCAN 4
 #define CRYS_OP_SORT 5
-#define CRYS_NUM_OPS 6
+#define CRYS_OP_TAGGED_SCAN 6
+#define CRYS_NUM_OPS 7
 /* Writes up to `max` (threads, items) pairs; returns the number of variants (or <0). */
 int crys_tile_variants(int op, int32_t* threads, int32_t* items, int32_t max);
 int crys_set_tile(int op, int32_t variant);

@@ -30,8 +30,9 @@ MAX_COLS, MAX_PREDS, MAX_JOINS, MAX_PLANS, MAX_FIELD_PREDS = 16, 8, 4, 32, 2
 ACCUMULATE = 1
 TAG_ANNOTATE = 2
 HASH_MULT, HASH_IDENT, HASH_DIRECT = 0, 1, 2
-OP_SELECT, OP_PROJECT, OP_PROBE, OP_PLAN, OP_SHARED_SCAN, OP_SORT = range(6)
-OP_NAMES = ["select", "project", "probe", "plan", "shared_scan", "sort"]
+OP_SELECT, OP_PROJECT, OP_PROBE, OP_PLAN, OP_SHARED_SCAN, OP_SORT, OP_TAGGED_SCAN = range(7)
+NUM_OPS = 7
+OP_NAMES = ["select", "project", "probe", "plan", "shared_scan", "sort", "tagged_scan"]
 
 
 class CrystalError(RuntimeError):

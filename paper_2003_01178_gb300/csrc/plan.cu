@@ -781,6 +781,10 @@ __global__ void __launch_bounds__(THREADS, (24 * kWarp) / THREADS > 0 ? (24 * kW
 // words so that one row's values in different regions do too.
 
 constexpr int kMaxTagPairs = 8;
+// Tagged-scan blocks resident per SM: two blocks of 512 threads (32 warps) measured
+// faster than three of 256, with the same shared memory left to each block's group
+// accumulators.
+constexpr int kTagBlocksPerSM = 2;
 constexpr int kMaxTagEntries = CRYS_MAX_PLANS * CRYS_MAX_JOINS;
 // A query's descriptor: kDescWords 32-bit fields (a column field holds the index of the
 // column's value region), stored field-major in shared memory: field f of query q at
@@ -1105,7 +1109,7 @@ __device__ __forceinline__ void tagged_scan_body(const TagHead& a, const int32_t
 }
 
 template <int THREADS, int ITEMS>
-__global__ void __launch_bounds__(THREADS, (24 * kWarp) / THREADS > 0 ? (24 * kWarp) / THREADS : 1)
+__global__ void __launch_bounds__(THREADS, kTagBlocksPerSM)
     tagged_scan_kernel(const __grid_constant__ TagArgs a) {
   // the head is read on every tile: a shared-memory copy is cheaper than the parameter
   // bank, whose cache does not hold a 9 KB argument block
@@ -1151,7 +1155,7 @@ __global__ void __launch_bounds__(256) prepare_kernel(const TagLaunch* __restric
 }
 
 template <int THREADS, int ITEMS>
-__global__ void __launch_bounds__(THREADS, (24 * kWarp) / THREADS > 0 ? (24 * kWarp) / THREADS : 1)
+__global__ void __launch_bounds__(THREADS, kTagBlocksPerSM)
     tagged_scan_kernel_dev(const TagArgs* __restrict__ a) {
   // the head is read on every tile: one shared-memory copy per block
   __shared__ __align__(16) TagHead head;
@@ -1618,7 +1622,7 @@ int64_t assign_accumulators(TagArgs& S, const DevQuery* q, size_t budget) {
   return used;
 }
 
-constexpr size_t kTagShare = (220u * 1024u) / kScanBlocksPerSM;  // shared memory of one block
+constexpr size_t kTagShare = (220u * 1024u) / kTagBlocksPerSM;  // shared memory of one block
 
 template <int THREADS, int ITEMS>
 int launch_tagged(TagBatch& tb, const DevQuery* q, unsigned char* scratch, cudaStream_t s) {
@@ -1896,7 +1900,7 @@ int crys_run_plans_tagged(const crys_table* fact, const crys_plan* plans, int32_
     for (int qi = 0; qi < n_plans && rc == CRYS_OK; ++qi) rc = zero_outputs(q[qi], s);
   if (rc == CRYS_OK && n_plans > 0 && row_end > row_begin) {
     unsigned char* base = static_cast<unsigned char*>(scratch);
-    constexpr int kOp = CRYS_OP_SHARED_SCAN;
+    constexpr int kOp = CRYS_OP_TAGGED_SCAN;
     switch (tile_variant(kOp)) {
       case 1: rc = launch_tagged<kTiles[kOp][1].threads, kTiles[kOp][1].items>(*tb, q, base, s); break;
       case 2: rc = launch_tagged<kTiles[kOp][2].threads, kTiles[kOp][2].items>(*tb, q, base, s); break;
@@ -1947,7 +1951,7 @@ int crys_tagged_prepare(const crys_table* fact, const crys_plan* plans, int32_t 
   }
   if (rc == CRYS_OK) {
     unsigned char* base = static_cast<unsigned char*>(scratch);
-    constexpr int kOp = CRYS_OP_SHARED_SCAN;
+    constexpr int kOp = CRYS_OP_TAGGED_SCAN;
     const int v = tile_variant(kOp);
     switch (v) {
       case 1: rc = prepare_block<kTiles[kOp][1].threads, kTiles[kOp][1].items>(*tb, q, base, out); break;
@@ -1984,7 +1988,7 @@ int crys_tagged_launch(const void* dev_block, crys_stream stream) {
   if (!dev_block || !aligned16(dev_block)) return CRYS_EINVAL;
   const TagLaunch* L = static_cast<const TagLaunch*>(dev_block);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  constexpr int kOp = CRYS_OP_SHARED_SCAN;
+  constexpr int kOp = CRYS_OP_TAGGED_SCAN;
   switch (tile_variant(kOp)) {
     case 1: return launch_block<kTiles[kOp][1].threads, kTiles[kOp][1].items>(L, s);
     case 2: return launch_block<kTiles[kOp][2].threads, kTiles[kOp][2].items>(L, s);

@@ -21,10 +21,11 @@ constexpr TileShape kTiles[CRYS_NUM_OPS][kMaxVariants] = {
     /* PROJECT     */ {{256, 16}, {256, 8}, {512, 8}, {128, 4}},
     /* PROBE       */ {{256, 16}, {256, 8}, {512, 8}, {128, 4}},
     /* PLAN        */ {{256, 8}, {512, 8}, {512, 4}, {128, 4}},
-    /* SHARED_SCAN */ {{256, 4}, {128, 8}, {128, 4}, {256, 8}},
+    /* SHARED_SCAN */ {{256, 4}, {256, 8}, {128, 8}, {128, 4}},
     /* SORT        */ {{512, 16}, {256, 16}, {256, 8}, {512, 8}},
+    /* TAGGED_SCAN */ {{512, 4}, {256, 4}, {128, 8}, {256, 8}},
 };
 
-constexpr int kNumVariants[CRYS_NUM_OPS] = {4, 4, 4, 4, 4, 4};
+constexpr int kNumVariants[CRYS_NUM_OPS] = {4, 4, 4, 4, 4, 4, 4};
 
 }  // namespace crys

@@ -30,7 +30,7 @@ import torch
 from . import (HashTable, crys_get_tile, crys_hash_build, crys_hash_init, crys_pack_fields, crys_run_plan,
                crys_run_plans_tagged, crys_run_plans_tagged_bytes, crys_tagged_block_bytes,
                crys_tagged_launch, crys_tagged_prepare, make_plan, make_table, capacity_for,
-               ACCUMULATE, MAX_PLANS, HASH_DIRECT, HASH_IDENT, OK, OP_SHARED_SCAN, TAG_ANNOTATE)
+               ACCUMULATE, MAX_PLANS, HASH_DIRECT, HASH_IDENT, OK, OP_TAGGED_SCAN, TAG_ANNOTATE)
 
 
 @dataclass
@@ -262,7 +262,7 @@ class ReplayedScan:
                                  scratch.numel(), self.host[i].data_ptr())
         if rc != OK:
             return False
-        shape = crys_get_tile(OP_SHARED_SCAN)
+        shape = crys_get_tile(OP_TAGGED_SCAN)
         if shape != self.shape:                 # a new tile shape: capture both graphs again
             for j in range(2):
                 if self.done[j] is not None:

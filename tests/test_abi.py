@@ -35,7 +35,7 @@ def test_every_declared_symbol_is_exported(crys):
 def test_strerror_and_tiles(crys):
     assert crys.strerror(crys.OK) == "ok"
     assert "argument" in crys.strerror(crys.EINVAL)
-    for op in range(6):
+    for op in range(crys.NUM_OPS):
         v = crys.crys_tile_variants(op)
         assert 1 <= len(v) <= 4 and all(t % 32 == 0 and i > 0 for t, i in v)
     assert crys.crys_tile_variants(0)[3] == (128, 4)      # the paper's tile shape is available

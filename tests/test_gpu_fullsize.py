@@ -25,7 +25,7 @@ def crys():
     _build.build()
     import paper_2003_01178_gb300 as crys
     crys.crys_device_errors(clear=True)
-    for op in range(6):
+    for op in range(crys.NUM_OPS):
         crys.crys_set_tile(op, 0)
     yield crys
     assert crys.crys_device_errors(clear=True) == 0

@@ -21,7 +21,7 @@ def crys():
     crys.crys_device_errors(clear=True)
     yield crys
     assert crys.crys_device_errors(clear=True) == 0
-    for op in range(6):
+    for op in range(crys.NUM_OPS):
         crys.crys_set_tile(op, 0)
 
 

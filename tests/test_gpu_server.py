@@ -94,15 +94,15 @@ def test_block_for_another_tile_shape_is_refused(store):
     hb = torch.empty(nb, dtype=torch.uint8, pin_memory=True)
     need = crys.crys_run_plans_tagged_bytes(ss.table, [cq.plan])
     scratch = ss.scratch(need)
-    crys.crys_set_tile(crys.OP_SHARED_SCAN, 0)
+    crys.crys_set_tile(crys.OP_TAGGED_SCAN, 0)
     assert crys.crys_tagged_prepare(ss.table, [cq.plan], 0, ss.n_rows, crys.TAG_ANNOTATE, [0], scratch,
                                     scratch.numel(), hb.data_ptr()) == crys.OK
     db = hb.cuda()
     before = cq.sums.clone()
-    crys.crys_set_tile(crys.OP_SHARED_SCAN, 2)           # another tile shape
+    crys.crys_set_tile(crys.OP_TAGGED_SCAN, 2)           # another tile shape
     crys.crys_tagged_launch(db)
     torch.cuda.synchronize()
-    crys.crys_set_tile(crys.OP_SHARED_SCAN, 0)
+    crys.crys_set_tile(crys.OP_TAGGED_SCAN, 0)
     assert crys.crys_device_errors(clear=True) & crys.DEV_BOUNDS
     assert torch.equal(cq.sums, torch.zeros_like(before))   # cleared by the prepare kernel only
 
@@ -120,13 +120,13 @@ def test_replayed_scan_follows_a_new_tile_shape(store, orc):
         mine = [ss.compile(q, zero=False) for q in queries]
     n = ss.n_rows
     try:
-        crys.crys_set_tile(crys.OP_SHARED_SCAN, 0)
+        crys.crys_set_tile(crys.OP_TAGGED_SCAN, 0)
         assert rep.launch(mine, 0, 100_000, list(range(10)))
-        crys.crys_set_tile(crys.OP_SHARED_SCAN, 1)
+        crys.crys_set_tile(crys.OP_TAGGED_SCAN, 1)
         assert rep.launch(mine, 100_000, n, [])
         stream.synchronize()
     finally:
-        crys.crys_set_tile(crys.OP_SHARED_SCAN, 0)
+        crys.crys_set_tile(crys.OP_TAGGED_SCAN, 0)
     assert crys.crys_device_errors(clear=True) == 0
     for c, q in zip(mine, queries):
         rs, rc = orc.ss_run(host, q)

@@ -24,7 +24,7 @@ def crys():
     crys.crys_device_errors(clear=True)
     yield crys
     assert crys.crys_device_errors(clear=True) == 0
-    for op in range(6):
+    for op in range(crys.NUM_OPS):
         crys.crys_set_tile(op, 0)
 
 
@@ -128,7 +128,7 @@ def _tagged(crys, w, plans, segments=((0, N),)):
 
 @pytest.mark.parametrize("variant", range(4))
 def test_tagged_matches_oracle_and_alone(crys, orc, world, variant):
-    crys.crys_set_tile(crys.OP_SHARED_SCAN, variant)
+    crys.crys_set_tile(crys.OP_TAGGED_SCAN, variant)
     qs = _queries(world)
     plans, outs = _plans(crys, qs)
     assert _tagged(crys, world, plans) > 0
@@ -140,7 +140,7 @@ def test_tagged_matches_oracle_and_alone(crys, orc, world, variant):
         assert np.array_equal(s.cpu().numpy(), rs) and np.array_equal(c.cpu().numpy(), rc)
         assert torch.equal(s, sa) and torch.equal(c, ca)
     crys.check_device_errors()
-    crys.crys_set_tile(crys.OP_SHARED_SCAN, 0)
+    crys.crys_set_tile(crys.OP_TAGGED_SCAN, 0)
 
 
 def test_tagged_segments_and_small_batches(crys, orc, world):
@@ -193,7 +193,7 @@ def test_tagged_every_fact_column_finishes(crys, orc, world, variant):
     """Every fact column is read by some query's predicates or aggregate (foreign-key
     columns included), through all four (column, table) pairs, with more than two fact
     predicates: each column is staged beside the pairs' values and read back from there."""
-    crys.crys_set_tile(crys.OP_SHARED_SCAN, variant)
+    crys.crys_set_tile(crys.OP_TAGGED_SCAN, variant)
     d0, d1, t0, t1 = world["d0"], world["d1"], world["t0"], world["t1"]
 
     def j(fk, table, dim, field, card, name, fps=()):
@@ -214,4 +214,4 @@ def test_tagged_every_fact_column_finishes(crys, orc, world, variant):
         rs, rc = orc.run_plan_raw(world["fact"], preds, [o for _, o in joins], agg)
         assert np.array_equal(s.cpu().numpy(), rs) and np.array_equal(c.cpu().numpy(), rc)
     crys.check_device_errors()
-    crys.crys_set_tile(crys.OP_SHARED_SCAN, 0)
+    crys.crys_set_tile(crys.OP_TAGGED_SCAN, 0)
