@@ -892,7 +892,8 @@ struct TagHead {
   int64_t row_begin, row_end;
   int32_t n_pairs;
   int32_t n_queries;
-  uint32_t all_mask;  // queries that can qualify at all
+  uint32_t all_mask;     // queries that can qualify at all
+  uint32_t global_mask;  // queries whose groups are added in global memory
   int32_t shared_groups;
   int32_t tile_shape;  // THREADS << 16 | ITEMS of the shape the arguments were prepared for
   int32_t smem_bytes;  // dynamic shared memory the launch provides
@@ -1066,19 +1067,27 @@ __device__ __forceinline__ void tagged_scan_body(const TagHead& a, const int32_t
       for (int i = 0; i < ITEMS; ++i) vals[(a.n_pairs + c) * PVS + i * THREADS + tid] = x[i];
     }
     __syncwarp();  // values of the warp's rows visible to all its lanes
-    // per item slot: expand each lane's (row, query) pairs into the warp's list, finish them
+    // per item slot: expand each lane's (row, query) pairs into the warp's list, finish them.
+    // Pairs of queries with shared-memory accumulators come first in the list and those
+    // with global ones after, so that all but one round take a single accumulation path.
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
-      const int n = __popc(rm[i]);
-      const int incl = warp_inclusive_scan(n, lane);
-      const int total = __shfl_sync(0xFFFFFFFFu, incl, kWarp - 1);
+      const uint32_t ms = rm[i] & ~a.global_mask, mg = rm[i] & a.global_mask;
+      const int ns = __popc(ms), ng = __popc(mg);
+      const int incl_s = warp_inclusive_scan(ns, lane), incl_g = warp_inclusive_scan(ng, lane);
+      const int total_s = __shfl_sync(0xFFFFFFFFu, incl_s, kWarp - 1);
+      const int total = total_s + __shfl_sync(0xFFFFFFFFu, incl_g, kWarp - 1);
       if (total == 0) continue;
       const int r = i * THREADS + tid;  // item-major index of the lane's row
       // the pairs go through the list in windows of L::LIST entries (one window unless
       // the round expands more pairs than that)
       for (int w0 = 0; w0 < total; w0 += L::LIST) {
-        int k = incl - n;
-        for (uint32_t m = rm[i]; m; m &= m - 1, ++k)
+        int k = incl_s - ns;
+        for (uint32_t m = ms; m; m &= m - 1, ++k)
+          if (k >= w0 && k < w0 + L::LIST)
+            list[k - w0] = static_cast<uint16_t>(((__ffs(m) - 1) << 11) | r);
+        k = total_s + incl_g - ng;
+        for (uint32_t m = mg; m; m &= m - 1, ++k)
           if (k >= w0 && k < w0 + L::LIST)
             list[k - w0] = static_cast<uint16_t>(((__ffs(m) - 1) << 11) | r);
         __syncwarp();
@@ -1619,6 +1628,9 @@ int64_t assign_accumulators(TagArgs& S, const DevQuery* q, size_t budget) {
     }
   }
   S.shared_groups = static_cast<int32_t>(used);
+  S.global_mask = 0;
+  for (int qi = 0; qi < S.n_queries; ++qi)
+    if (S.desc[kDAccMode * CRYS_MAX_PLANS + qi] == kAccGlobal) S.global_mask |= 1u << qi;
   return used;
 }
 
