@@ -794,14 +794,16 @@ constexpr int kMaxTagEntries = CRYS_MAX_PLANS * CRYS_MAX_JOINS;
 // that always pass, so every lane runs the same instructions whatever query it finishes.
 constexpr int kDescWords = 54;
 enum DescField : int {
-  kDAggA = 0, kDAggB = 1, kDAccMode = 2, kDAccOff = 3,       // group 0
-  kDP0Col = 4, kDP0Lo = 5, kDP0Span = 6, kDP1Col = 7,        // group 1: fact predicates 0, 1
-  kDP1Lo = 8, kDP1Span = 9, kDPreds = 10, kDGroups = 11,     // group 2
-  kDMulAB = 12, kDCoefA = 13, kDCoefB = 14,                  // group 3: val = a*b or ca*a + cb*b
-  kDGroup0 = 16,      // 4 groups of 4 words: pair << 8 | shift, mask, card, stride
-  kDSums = 32,        // 2 words, then counts (2 words)
+  kDAggA = 0, kDAggB = 1,                     // aggregate operands (value regions)
+  kDAccMode = 2, kDAccOff = 3,                // shared-memory accumulators (offset) or global
+  kDP0Col = 4, kDP0Lo = 5, kDP0Span = 6,      // fact predicate 0: region, lo, span
+  kDP1Col = 7, kDP1Lo = 8, kDP1Span = 9,      // fact predicate 1
+  kDPreds = 10, kDGroups = 11,                // fact predicates, grouped joins
+  kDMulAB = 12, kDCoefA = 13, kDCoefB = 14,   // val = a*b, or ca*a + cb*b
+  kDGroup0 = 16,      // 4 grouped joins of 4 words: pair << 8 | shift, mask, card, stride
+  kDSums = 32,        // output pointers: sums (2 words), then counts (2 words)
   kDCounts = 34,
-  kDMorePreds = 36,   // predicates 2..7: column, lo, span
+  kDMorePreds = 36,   // fact predicates 2..7: region, lo, span
 };
 static_assert(kDMorePreds + 3 * (CRYS_MAX_PREDS - 2) <= kDescWords, "descriptor fields");
 
