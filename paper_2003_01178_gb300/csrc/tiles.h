@@ -22,7 +22,7 @@ constexpr TileShape kTiles[CRYS_NUM_OPS][kMaxVariants] = {
     /* PROBE       */ {{256, 16}, {256, 8}, {512, 8}, {128, 4}},
     /* PLAN        */ {{256, 8}, {512, 8}, {512, 4}, {128, 4}},
     /* SHARED_SCAN */ {{256, 4}, {256, 8}, {128, 8}, {128, 4}},
-    /* SORT        */ {{512, 16}, {256, 16}, {256, 8}, {512, 8}},
+    /* SORT        */ {{256, 32}, {256, 24}, {512, 16}, {256, 16}},
     /* TAGGED_SCAN */ {{512, 4}, {256, 4}, {128, 8}, {256, 8}},
 };
 
