@@ -305,6 +305,10 @@ def run_served(args, rank, world, local):
     # filtered builds + one fused probe kernel) and the same kernel on the resident tables
     if not args.quick:
         out["one_at_a_time"] = {}
+        # the single-query kernel gets its own tuned tile shape, as the shared scan did
+        plan_cqs = [store.compile(q, mode="resident") for q in batch_queries(seed, 20_001, rank)[:8]]
+        out["one_at_a_time"]["tile"] = autotune(crys.OP_PLAN, lambda: [store.run(c) for c in plan_cqs], args)
+        del plan_cqs
         for mode in ("filtered", "resident"):
             alone_ms = []
             for s in range(min(args.steps, 3)):
