@@ -347,3 +347,50 @@ def test_plan_rejects_bad_group_codes(orc):
               "group": np.array([0, 9], np.int32), "card": 3}]
     with pytest.raises(ValueError):
         orc.run_plan_raw(cols, [], joins, ("sum", 1, None))
+
+
+def _brute_served(t, q):
+    """A served query evaluated row by row from its dict: dimension rows looked up by key,
+    filters and group attributes read by name, group id mixed-radix with the first grouped
+    join most significant, the SUM expression by its operand names."""
+    fact, dims = t["fact"], t["dims"]
+    by_key = {d: {int(k): r for r, k in enumerate(cols["key"])} for d, cols in dims.items()}
+    grouped = [j for j in q["joins"] if j["group"] is not None]
+    cards = [datagen.SS_DIMS[j["dim"]]["attrs"][j["group"]] for j in grouped]
+    n_groups = int(np.prod(cards)) if cards else 1
+    sums, counts = [0] * n_groups, [0] * n_groups
+    op, a, b = q["agg"]
+    for i in range(fact["qty"].size):
+        if not all(lo <= int(fact[c][i]) <= hi for c, lo, hi in q["fact_preds"]):
+            continue
+        codes, ok = {}, True
+        for j in q["joins"]:
+            r = by_key[j["dim"]].get(int(fact[datagen.SS_DIMS[j["dim"]]["fk"]][i]))
+            if r is None or not all(lo <= int(dims[j["dim"]][at][r]) <= hi for at, lo, hi in j["filters"]):
+                ok = False
+                break
+            if j["group"] is not None:
+                codes[id(j)] = int(dims[j["dim"]][j["group"]][r])
+        if not ok:
+            continue
+        g = 0
+        for j, card in zip(grouped, cards):
+            g = g * card + codes[id(j)]
+        x = int(fact[a][i])
+        y = int(fact[b][i]) if b is not None else 0
+        sums[g] += {"sum": x, "mul": x * y, "sub": x - y, "add": x + y}[op]
+        counts[g] += 1
+    return sums, counts
+
+
+def test_served_query_brute_force(orc):
+    # queries of the seeded stream on a small star schema, each computed from its dict
+    t = datagen.ss_tables(23, 4000, dim_scale=0.004)
+    checked = 0
+    for qid in range(60):
+        q = datagen.ss_query(23, qid)
+        bs, bc = _brute_served(t, q)
+        s, c = orc.ss_run(t, q)
+        assert s.tolist() == bs and c.tolist() == bc, q
+        checked += sum(bc) > 0
+    assert checked >= 10          # enough of them select rows for the comparison to bite
