@@ -204,16 +204,28 @@ def graph_differential_ms(fn, flush, k=20, rounds=7):
 # ----------------------------------------------------------------------------- served
 
 def served_store(seed, n_rows, dim_scale, device):
+    import datagen
     import datagen.device as dgd
-    from paper_2003_01178_gb300.starschema import ResidentStarSchema, served_schema
+    from paper_2003_01178_gb300.starschema import ResidentStarSchema, Schema
     t = dgd.ss_tables(seed, n_rows, device, dim_scale)
-    return ResidentStarSchema(served_schema(), t["fact"], t["dims"])
+    return ResidentStarSchema(Schema.from_spec(datagen.SS_FACT_COLS, datagen.SS_DIMS), t["fact"], t["dims"])
 
 
 def batch_queries(seed, step, rank=0):
     import datagen
     base = (rank * 100_000) + step * BATCH
     return [datagen.ss_query(seed, base + i) for i in range(BATCH)]
+
+
+def served_config(args, world):
+    """The served workload's config, identical in both arms of the bench."""
+    return {"workload": f"served star-schema stream: fact {args.rows // 1_000_000}M rows x 8 int32 cols "
+                        f"({args.rows * 32 / 1e9:.1f} GB), dims 2556/200K/3M/1.4M rows, batches of {BATCH} "
+                        "seeded select-join-group-by queries (1-4 joins, selectivity 1e-4..0.5, <=1e4 groups, "
+                        "int64 sums)",
+            "fact_rows": args.rows, "batch_queries": BATCH, "seed": args.seed,
+            "l2": "inputs larger than L2 (the fact table is read whole by every step)",
+            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"}
 
 
 def run_served(args, rank, world, local):
@@ -277,18 +289,12 @@ def run_served(args, rank, world, local):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(elapsed_ms / args.steps, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
         "data": "synthetic (seeded counter-based generator, generated in HBM)",
-        "config": {"workload": f"served star-schema stream: fact 600M rows x 8 int32 cols (19.2 GB), "
-                               f"dims 2556/200K/3M/1.4M rows, batches of {BATCH} seeded select-join-group-by "
-                               f"queries (1-4 joins, selectivity 1e-4..0.5, <=1e4 groups, int64 sums)",
-                   "fact_rows": store.n_rows, "batch_queries": BATCH,
-                   "step": f"compile {BATCH} queries against the resident direct dimension tables + one tagged "
-                           "shared scan of the fact table: annotate_kernel tags every dimension row with "
-                           "the bitmap of the batch's queries it satisfies, tagged_scan_kernel reads one "
-                           "tag per dimension and fact row and finishes only the qualifying (row, query) "
-                           "pairs; the query dicts (workload input) are generated before the timed region",
-                   "l2": "inputs larger than L2 (19.2 GB fact table per scan)",
-                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                   "tile": tile},
+        "config": served_config(args, world), "tile": tile,
+        "step_detail": f"compile {BATCH} queries against the resident direct dimension tables + one tagged "
+                       "shared scan of the fact table: annotate_kernel tags every dimension row with "
+                       "the bitmap of the batch's queries it satisfies, tagged_scan_kernel reads one "
+                       "tag per dimension and fact row and finishes only the qualifying (row, query) "
+                       "pairs; the query dicts (workload input) are generated before the timed region",
         "scanned_gbs": {"aggregate": round(scanned_gbs, 1),
                         "per_query_mean_gb": round(sum(per_query_bytes) / len(per_query_bytes) / 1e9, 3),
                         "note": "sum over queries of each query's own column bytes / wall time"},
@@ -297,7 +303,7 @@ def run_served(args, rank, world, local):
     achieved = scan_bytes / (avg_scan_ms / 1e3) / 1e9
     out["roofline"] = {"kernel": "tagged_scan_kernel", "bound": "hbm", "achieved": round(achieved, 1),
                        "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                       "peak_source": peak_kind, "traffic": traffic_for("tagged_scan_kernel", args),
+                       "peak_source": peak_kind, "traffic": traffic_for("tagged_scan_kernel", "served"),
                        "algorithmic_bytes_per_launch": scan_bytes, "avg_launch_ms": round(avg_scan_ms, 4),
                        "timed": "one shared-scan call per batch on its stream: annotate_kernel + "
                                 "tagged_scan_kernel"}
@@ -332,6 +338,8 @@ def run_served(args, rank, world, local):
         out["e2e"] = {"value": out["served"]["closed_loop_qps"], "unit": "queries/s",
                       "h2d_bytes_per_step": out["served"]["h2d_bytes_per_batch"],
                       "d2h_bytes_per_step": out["served"]["d2h_bytes_per_batch"],
+                      "bytes_counted": "from the tensors copied in the closed loop, per batch of "
+                                       f"{BATCH} queries",
                       "what": "public serving API, closed loop: query dicts in from the host, plans "
                               "compiled, each launch's argument block copied from pinned host memory "
                               "(h2d), circular tagged shared scans replayed from CUDA graphs, int64 "
@@ -340,6 +348,9 @@ def run_served(args, rank, world, local):
     out["clocks"] = clocks.summary()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline_served(store, args)
+    if not args.no_operators and not args.quick:
+        # configs 1-4 at their stated sizes on the same GPU (the served store stays resident)
+        out["operators"] = run_operators_block(args, dev, stream)
         out["paper_context"] = {
             "note": "the paper's figures, for context only (other hardware, other baselines)",
             "bandwidth_ratio": "16.2x: V100 (880 GB/s) over i7-6900 (about 54 GB/s), Section 4",
@@ -347,11 +358,6 @@ def run_served(args, rank, world, local):
             "this_run_gpu_over_oracle": round(out["value"] / out["cpu_baseline"]["value"], 1)
             if out["cpu_baseline"]["value"] else None}
     return out
-
-
-def crys_block_bytes():
-    import paper_2003_01178_gb300 as crys
-    return crys.crys_tagged_block_bytes()
 
 
 def served_loop(store, args, rank):
@@ -373,7 +379,7 @@ def served_loop(store, args, rank):
         _, st = server.serve(queries, datagen.ss_arrivals(args.seed + 1, n, r), realtime=True)
         curve.append({"offered_qps": round(r, 1), "served_qps": round(st.qps, 1),
                       "p50_ms": round(st.percentile_ms(50), 2), "p99_ms": round(st.percentile_ms(99), 2)})
-    groups = sum(store.groups(q) for q in queries)
+    batches = max(1.0, st_closed.completed / BATCH)
     return {"closed_loop_qps": round(st_closed.qps, 2), "open_loop_offered_qps": round(rate, 2),
             "open_loop_qps": round(st_open.qps, 2),
             "p50_ms": round(st_open.percentile_ms(50), 3), "p99_ms": round(st_open.percentile_ms(99), 3),
@@ -385,9 +391,10 @@ def served_loop(store, args, rank):
             "graph_replays": st_open.replays + st_closed.replays,
             "launch": "each launch replays a captured CUDA graph {pinned argument block -> device, "
                       "prepare_kernel, tagged_scan_kernel_dev}",
-            # per batch of 32 queries: one pinned argument block copied to the device per launch
-            "h2d_bytes_per_batch": int(crys_block_bytes() * st_closed.launches / max(1, n / BATCH)),
-            "d2h_bytes_per_batch": int(16 * groups / n * BATCH)}
+            # bytes the closed loop copied (argument blocks in, int64 results out), per batch
+            "h2d_bytes_per_batch": int(st_closed.h2d_bytes / batches),
+            "d2h_bytes_per_batch": int(st_closed.d2h_bytes / batches),
+            "peak_held_bytes": st_closed.peak_held_bytes}
 
 
 def oracle_threads():
@@ -395,48 +402,68 @@ def oracle_threads():
     return oracle.hardware_threads()
 
 
-def oracle_query_seconds(host, query, sample_rows, full_rows, threads):
-    """Time of the oracle (as it stands) for one query over `full_rows` fact rows,
-    extrapolated from two timed runs: over 0 rows (its fixed cost: indexing the
-    dimension tables) and over the first `sample_rows` rows (t = fixed + rows * per_row)."""
+def time_oracle_query(host, query, threads, fact_rows=None):
+    """Wall seconds of the oracle (as it stands) for one served query."""
     import oracle
     t0 = time.perf_counter()
-    oracle.ss_run(host, query, threads=threads, fact_rows=0)
-    fixed = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    oracle.ss_run(host, query, threads=threads, fact_rows=sample_rows)
-    sampled = time.perf_counter() - t0
-    per_row = max(0.0, sampled - fixed) / sample_rows
-    return fixed + per_row * full_rows, fixed + sampled
+    oracle.ss_run(host, query, threads=threads, fact_rows=fact_rows)
+    return time.perf_counter() - t0
 
 
 def cpu_baseline_served(store, args):
-    """The oracle (plain row-at-a-time C, rows split over all host threads) on a bounded
-    sample: a few queries of the first batch, each timed over 0 and over the first
-    `cpu_sample_rows` fact rows, extrapolated to the full table."""
-    rows = min(args.cpu_sample_rows, store.n_rows)
-    host = {"fact": {c: store.fact[c][:rows].cpu().numpy() for c in store.schema.fact_cols},
+    """The oracle (plain row-at-a-time C, rows split over all host threads) timed over ALL
+    fact rows for the first `cpu_queries` queries of the first batch; a linear
+    extrapolation from the first 2M rows is kept beside it as a cross-check."""
+    host = {"fact": {c: store.fact[c].cpu().numpy() for c in store.schema.fact_cols},
             "dims": {d: {k: v.cpu().numpy() for k, v in t.items()} for d, t in store.dims.items()}}
     threads = oracle_threads()
     qs = batch_queries(args.seed, 0)[: args.cpu_queries]
-    full, spent = 0.0, 0.0
+    full = [time_oracle_query(host, q, threads) for q in qs]
+    sample = min(2_000_000, store.n_rows)
+    extrap = []
     for q in qs:
-        f, sp = oracle_query_seconds(host, q, rows, store.n_rows, threads)
-        full += f
-        spent += sp
-    return {"value": round(len(qs) / full, 4), "unit": "queries/s", "cores": threads, "kind": "oracle",
-            "sample": f"{len(qs)} queries of the first batch, each timed over 0 and over the first {rows} "
-                      f"of {store.n_rows} fact rows and extrapolated linearly to all rows ({spent:.1f} s spent)"}
+        fixed = time_oracle_query(host, q, threads, fact_rows=0)
+        part = time_oracle_query(host, q, threads, fact_rows=sample)
+        extrap.append(fixed + max(0.0, part - fixed) / sample * store.n_rows)
+    del host
+    return {"value": round(len(qs) / sum(full), 4), "unit": "queries/s", "cores": threads, "kind": "oracle",
+            "sample": f"{len(qs)} queries of the first batch, each timed over all {store.n_rows} fact rows "
+                      f"({sum(full):.1f} s of oracle time)",
+            "seconds_per_query": [round(t, 3) for t in full],
+            "cross_check_extrapolated_from_2M_rows": round(len(qs) / sum(extrap), 4)}
+
+
+def host_star_schema(seed, rows, dim_scale, threads):
+    """Host copy of the served star schema, generated in row chunks on `threads` threads
+    (the generator is a pure function of (seed, stream, row), so chunks are independent)."""
+    from concurrent.futures import ThreadPoolExecutor
+    import datagen
+    chunk = 1 << 24
+    fact = {c: np.empty(rows, dtype=np.int32) for c in datagen.SS_FACT_COLS}
+
+    def fill(job):
+        c, b = job
+        e = min(rows, b + chunk)
+        fact[c][b:e] = datagen.ss_fact_col(seed, c, e - b, start=b, dim_scale=dim_scale)
+    with ThreadPoolExecutor(max(1, threads)) as ex:
+        list(ex.map(fill, [(c, b) for c in datagen.SS_FACT_COLS for b in range(0, rows, chunk)]))
+    dims = {d: datagen.ss_dimension(seed, d, dim_scale) for d in datagen.SS_DIMS}
+    return {"fact": fact, "dims": dims}
 
 
 # ----------------------------------------------------------------------------- operators
+#
+# Configs 1-4 (Section 4 microbenchmarks and the fused query of Section 5.3), each timed
+# by one function that returns a plain dict: milliseconds, algorithmic GB/s against the
+# measured HBM peak, and the tile shape the tuner chose.  The default run puts them all in
+# an "operators" block of the served line; ``--workload <name>`` prints one as its own line.
 
 KERNEL_FILES = {"select_kernel": "select.cu", "project_kernel": "project.cu", "probe_kernel": "hash.cu",
                 "sort_pass_kernel": "sort.cu", "plan_kernel": "plan.cu", "tagged_scan_kernel": "plan.cu",
                 "shared_scan_kernel": "plan.cu"}
 
 
-def traffic_for(kernel, args):
+def traffic_for(kernel, workload):
     """DRAM bytes per launch from the committed ncu summary, if it was taken on the
     current source of the kernel; else None."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
@@ -445,7 +472,7 @@ def traffic_for(kernel, args):
         with open(path) as f:
             for line in f:
                 parts = line.split()
-                if len(parts) >= 4 and parts[0] == kernel and parts[1] == args.workload and parts[2] == src_hash:
+                if len(parts) >= 4 and parts[0] == kernel and parts[1] == workload and parts[2] == src_hash:
                     return int(parts[3])
     except Exception:
         pass
@@ -464,21 +491,12 @@ def kernel_source_hash(kernel):
     return h.hexdigest()[:12]
 
 
-def op_line(args, world, name, value, unit, kernel, alg_bytes, avg_ms, config, extra=None):
-    peak, kind = measured_hbm_peak()
-    achieved = alg_bytes / (avg_ms / 1e3) / 1e9
-    out = {"metric": METRIC, "value": round(value, 2), "unit": unit, "n_gpus": world,
-           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(avg_ms, 4),
-           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-           "dtype": config.pop("dtype", "int32"), "data": "synthetic (seeded counter-based generator)",
-           "config": dict(workload=name, **config),
-           "roofline": {"kernel": kernel, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
-                        "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_source": kind,
-                        "traffic": traffic_for(kernel, args), "algorithmic_bytes_per_launch": int(alg_bytes),
-                        "avg_launch_ms": round(avg_ms, 4)}}
-    if extra:
-        out.update(extra)
-    return out
+def gbs(alg_bytes, ms):
+    return alg_bytes / (ms / 1e3) / 1e9
+
+
+def frac(alg_bytes, ms):
+    return round(gbs(alg_bytes, ms) / measured_hbm_peak()[0], 4)
 
 
 def autotune(op, launch, args):
@@ -513,173 +531,265 @@ def time_launches(fn, steps, warmup, stream, flush=None):
     return ms
 
 
-def run_operator(args, rank, world, local):
+def op_select(args, dev, stream, strawman=True):
+    """Config 2(1): selection of 2^29 int32 uniform in [0, 2^31), x < v, sigma 0..1."""
     import torch
     import datagen
     import datagen.device as dgd
     import paper_2003_01178_gb300 as crys
+    n = args.rows or (1 << 29)
+    x = dgd.uniform_i32(args.seed, datagen.STREAMS["sel.x"], n, 0, (1 << 31) - 1, dev)
+    out = torch.empty(n, dtype=torch.int32, device=dev)
+    cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+    his = [datagen.select_threshold(i / 10) for i in range(11)]
+
+    def whole_sweep():  # the metric is the mean over the sweep, so tune on all of it
+        for hi in his:
+            crys.crys_select(x, n, -(1 << 31), hi, out, cnt, 0)
+    tile = autotune(crys.OP_SELECT, whole_sweep, args)
+    sweep = {}
+    for sigma in [i / 10 for i in range(11)]:
+        hi = datagen.select_threshold(sigma)
+        ms = time_launches(lambda: crys.crys_select(x, n, -(1 << 31), hi, out, cnt, 0), args.steps, args.warmup, stream)
+        sweep[f"{sigma:.1f}"] = statistics.median(ms)
+    avg = statistics.mean(sweep.values())
+    alg = statistics.mean([4 * n * (1 + float(s)) for s in sweep])
+    res = {"kernel": "select_kernel", "rows": n, "ms_mean": round(avg, 4), "alg_bytes_mean": int(alg),
+           "GB/s": round(gbs(alg, avg), 1), "frac": frac(alg, avg),
+           "ms_at_0.5": round(sweep["0.5"], 4), "frac_at_0.5": frac(4 * n * 1.5, sweep["0.5"]),
+           "sweep_ms": {k: round(v, 4) for k, v in sweep.items()}, "tile": tile,
+           "bytes": "4N read + 4 sigma N written (Section 4.2 model)"}
+    if strawman:
+        # the independent-threads selection the paper compares against (ablation)
+        stb = crys.crys_select_strawman(None, n, -(1 << 31), 0, None, None, None, -1)
+        stemp = crys.scratch(stb, dev)
+        straw = {}
+        for sigma in (0.0, 0.5, 1.0):
+            hi = datagen.select_threshold(sigma)
+            ms = time_launches(lambda: crys.crys_select_strawman(x, n, -(1 << 31), hi, out, cnt, stemp, stb),
+                               args.steps, args.warmup, stream)
+            straw[f"{sigma:.1f}"] = round(statistics.median(ms), 4)
+        res["independent_threads"] = {
+            "ms": straw, "slowdown_at_0.5": round(straw["0.5"] / sweep["0.5"], 2),
+            "paper": "19 ms independent threads vs 2.1 ms tile-based, V100, 2^29 rows, sigma 0.5 (Section 3.2)"}
+    del x, out
+    return res
+
+
+def op_project(args, dev, stream):
+    """Config 2(2): y = 2 x1 + 3 x2 and its sigmoid over 2^29 float32 rows."""
+    import torch
+    import datagen
+    import datagen.device as dgd
+    import paper_2003_01178_gb300 as crys
+    n = args.rows or (1 << 29)
+    x1 = dgd.uniform_f32(args.seed, datagen.STREAMS["proj.x1"], n, dev)
+    x2 = dgd.uniform_f32(args.seed, datagen.STREAMS["proj.x2"], n, dev)
+    y = torch.empty_like(x1)
+    tile = autotune(crys.OP_PROJECT, lambda: crys.crys_project(x1, x2, n, 2.0, 3.0, crys.PROJ_LINEAR, y), args)
+    ms = {}
+    for op, nm in ((crys.PROJ_LINEAR, "linear"), (crys.PROJ_SIGMOID, "sigmoid")):
+        ms[nm] = statistics.median(time_launches(lambda: crys.crys_project(x1, x2, n, 2.0, 3.0, op, y),
+                                                 args.steps, args.warmup, stream))
+    avg = statistics.mean(ms.values())
+    del x1, x2, y
+    return {"kernel": "project_kernel", "rows": n, "ms_mean": round(avg, 4), "alg_bytes": 12 * n,
+            "GB/s": round(gbs(12 * n, avg), 1), "frac": frac(12 * n, avg),
+            "ms": {k: round(v, 4) for k, v in ms.items()},
+            "frac_by_op": {k: frac(12 * n, v) for k, v in ms.items()}, "tile": tile,
+            "bytes": "8N read + 4N written (Section 4.1 model)"}
+
+
+def op_q1(args, dev, stream, sizes):
+    """Config 1: the fused filter-probe-aggregate query (yr == 3 AND a < 25 AND 1 <= b <= 3,
+    SUM(c * b)) at each fact size, L2 flushed before every timed launch."""
+    import torch
+    import datagen.device as dgd
+    import paper_2003_01178_gb300 as crys
+    flush_buf = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    out = {}
+    for n in sizes:
+        t = dgd.q1_tables(args.seed, n, dev)
+        f, d = t["fact"], t["dim"]
+        ht = crys.HashTable.build(d["key"], d["yr"], filters=[(d["yr"], 3, 3)])
+        sums = torch.zeros(1, dtype=torch.int64, device=dev)
+        cnts = torch.zeros(1, dtype=torch.int64, device=dev)
+        table = crys.make_table([f["fk"], f["a"], f["b"], f["c"]])
+        plan = crys.make_plan([(1, -(1 << 31), 24), (2, 1, 3)], [(0, ht, 0)], ("mul", 3, 2), sums, cnts)
+        tile = autotune(crys.OP_PLAN, lambda: (l2_flush(flush_buf), crys.crys_run_plan(table, plan)), args)
+        ms = statistics.median(time_launches(lambda: crys.crys_run_plan(table, plan), args.steps, args.warmup,
+                                             stream, flush=lambda: l2_flush(flush_buf)))
+        graphed = graph_differential_ms(lambda: crys.crys_run_plan(table, plan), lambda: l2_flush(flush_buf))
+        out[str(n)] = {"ms": round(ms, 4), "GB/s": round(gbs(16 * n, ms), 1), "frac": frac(16 * n, ms),
+                       "graph_ms": round(graphed, 4),
+                       "graph_frac": frac(16 * n, graphed) if graphed > 0 else None, "tile": tile}
+        del t, f, d, ht, table, plan
+    del flush_buf
+    return {"kernel": "plan_kernel", "by_rows": out, "bytes": "16 B per fact row: 4 columns (Section 3.1 bound)",
+            "l2": "flushed before each timed launch (512 MB write)",
+            "graph_ms_note": "per-launch device time from CUDA-graph replays of k x {L2 flush, kernel} minus "
+                             "k x {L2 flush}: no launch or event overhead"}
+
+
+def op_sort(args, dev, stream):
+    """Config 4: radix sort of 2^28 (key, row id) pairs."""
+    import torch
+    import datagen
+    import datagen.device as dgd
+    import paper_2003_01178_gb300 as crys
+    n = args.rows or (1 << 28)
+    keys = dgd.bits_i32(args.seed, datagen.STREAMS["sort.key"], n, dev)
+    vals = torch.arange(n, dtype=torch.int32, device=dev)
+    ko, vo = torch.empty_like(keys), torch.empty_like(vals)
+    tb = crys.crys_sort(None, None, None, None, n, None, -1)
+    temp = crys.scratch(tb, dev)
+    tile = autotune(crys.OP_SORT, lambda: crys.crys_sort(keys, vals, ko, vo, n, temp, tb), args)
+    ms = statistics.median(time_launches(lambda: crys.crys_sort(keys, vals, ko, vo, n, temp, tb),
+                                         args.steps, args.warmup, stream))
+    res = {"kernel": "sort_pass_kernel", "rows": n, "lsd_stable": {
+        "ms": round(ms, 4), "Mkeys/s": round(n / (ms / 1e3) / 1e6, 1), "GB/s": round(gbs(68 * n, ms), 1),
+        "frac": frac(68 * n, ms), "tile": tile,
+        "bytes": "one 4N key read for all digit histograms + 4 passes x (8N read + 8N written) = 68N"},
+        "paper": "V100: 27.08 ms for 2^28 key+value pairs, unstable MSB sort (Section 4.4)"}
+    del keys, vals, ko, vo, temp
+    return res
+
+
+def op_join(args, dev, stream, sizes, partial=True):
+    """Config 3: build N unique keys at 50% fill, probe 2^28 foreign keys, SUM(payload * value)."""
+    import torch
+    import datagen
+    import datagen.device as dgd
+    import paper_2003_01178_gb300 as crys
+    n_probe = args.rows or (1 << 28)
+    res = {}
+    l2_bytes = int(getattr(torch.cuda.get_device_properties(dev), "L2_cache_size", 126 << 20))
+    pay = dgd.uniform_i32(args.seed, datagen.STREAMS["join.pay"], n_probe, 1, 100, dev)
+    for lg in sizes:
+        nb = 1 << lg
+        bk = dgd.perm_i32(args.seed, datagen.STREAMS["join.bkey"], nb, dev)
+        bv = dgd.uniform_i32(args.seed, datagen.STREAMS["join.bval"], nb, 1, 100, dev)
+        ht = crys.HashTable.build(bk, bv)
+        fk = dgd.uniform_i32(args.seed, datagen.STREAMS["join.fk"], n_probe, 0, nb - 1, dev)
+        s = torch.zeros(2, dtype=torch.int64, device=dev)
+        tile = autotune(crys.OP_PROBE, lambda: crys.crys_probe_aggregate(fk, pay, n_probe, ht.struct, s[0:1], s[1:2]),
+                        args)
+        pm = statistics.median(time_launches(
+            lambda: crys.crys_probe_aggregate(fk, pay, n_probe, ht.struct, s[0:1], s[1:2]), args.steps, args.warmup,
+            stream))
+        bms = statistics.median(time_launches(
+            lambda: (crys.crys_hash_init(ht.struct), crys.crys_hash_build(bk, bv, nb, [], ht.struct)),
+            max(1, args.steps // 2), 1, stream))
+        # Section 4.3 model: the probe scan plus, for each probe that misses L2 (hit share
+        # pi = L2 size / table size, at most 1), the line a miss fills: 32 B in the paper's
+        # sector reading, 128 B as measured on this GPU (every random miss fills a whole
+        # 128-byte line; see the probe_kernel locality summary)
+        pi = min(1.0, l2_bytes / ht.nbytes)
+        model32 = 8 * n_probe + (1.0 - pi) * n_probe * 32
+        model128 = 8 * n_probe + (1.0 - pi) * n_probe * 128
+        res[f"2^{lg}"] = {"probe_ms": round(pm, 4), "build_ms": round(bms, 4),
+                          "table_mb": round(ht.nbytes / 2 ** 20, 3), "tile": tile,
+                          "model_bytes": int(model32), "model_frac": frac(model32, pm),
+                          "model_bytes_128B_lines": int(model128), "model_frac_128B_lines": frac(model128, pm)}
+        del ht, bk, bv, fk
+    out = {"kernel": "probe_kernel", "probe_rows": n_probe, "fill": "50%", "sweep": res, "l2_bytes": l2_bytes,
+           "note": "model bytes = probe scan 8|P| + (1 - pi)|P| x line, pi = min(1, L2 / table) (Section 4.3 "
+                   "model); line = 32 B (sector) or 128 B (the line a random miss fills on this GPU)"}
+    if partial:
+        # partial matches on the largest table: probe keys spread over [0, N / pi), so a
+        # share pi of them finds its key (the others read a slot and miss)
+        lg = sizes[-1]
+        nb = 1 << lg
+        bk = dgd.perm_i32(args.seed, datagen.STREAMS["join.bkey"], nb, dev)
+        bv = dgd.uniform_i32(args.seed, datagen.STREAMS["join.bval"], nb, 1, 100, dev)
+        ht = crys.HashTable.build(bk, bv)
+        part = {}
+        for pi in (0.5, 0.1):
+            fk = dgd.uniform_i32(args.seed, datagen.STREAMS["join.fk"], n_probe, 0, int(nb / pi) - 1, dev)
+            s = torch.zeros(2, dtype=torch.int64, device=dev)
+            ms = time_launches(lambda: crys.crys_probe_aggregate(fk, pay, n_probe, ht.struct, s[0:1], s[1:2]),
+                               args.steps, args.warmup, stream)
+            part[f"{pi}"] = {"probe_ms": round(statistics.median(ms), 4),
+                             "matched": round(int(s[1].item()) / n_probe, 4)}
+            del fk
+        out["partial_match_largest_table"] = part
+        del ht, bk, bv
+    del pay
+    return out
+
+
+def run_operators_block(args, dev, stream):
+    """Every operator config at its stated size, with its own clock record."""
+    import torch
+    ops = {}
+    with ClockSampler(dev.index if dev.index is not None else 0) as clocks:
+        ops["q1"] = op_q1(args, dev, stream, [1 << 22, 1 << 28])
+        ops["select"] = op_select(args, dev, stream)
+        ops["project"] = op_project(args, dev, stream)
+        ops["sort"] = op_sort(args, dev, stream)
+        ops["join"] = op_join(args, dev, stream, [10, 22, 27], partial=False)
+        torch.cuda.synchronize(dev)
+    ops["clocks"] = clocks.summary()
+    ops["peak_gbs"], ops["peak_source"] = measured_hbm_peak()
+    return ops
+
+
+def op_line(args, world, name, value, unit, kernel, alg_bytes, avg_ms, config, extra=None):
+    peak, kind = measured_hbm_peak()
+    achieved = alg_bytes / (avg_ms / 1e3) / 1e9
+    out = {"metric": METRIC, "value": round(value, 2), "unit": unit, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(avg_ms, 4),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": config.pop("dtype", "int32"), "data": "synthetic (seeded counter-based generator)",
+           "config": dict(workload=name, **config),
+           "roofline": {"kernel": kernel, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                        "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_source": kind,
+                        "traffic": traffic_for(kernel, name), "algorithmic_bytes_per_launch": int(alg_bytes),
+                        "avg_launch_ms": round(avg_ms, 4)}}
+    if extra:
+        out.update(extra)
+    return out
+
+
+def run_operator(args, rank, world, local):
+    import torch
+    import paper_2003_01178_gb300 as crys
 
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
-    seed = args.seed
     launches0 = crys.crys_launch_count()
     with ClockSampler(local) as clocks:
         if args.workload == "select":
-            n = args.rows or (1 << 29)
-            x = dgd.uniform_i32(seed, datagen.STREAMS["sel.x"], n, 0, (1 << 31) - 1, dev)
-            out = torch.empty(n, dtype=torch.int32, device=dev)
-            cnt = torch.zeros(1, dtype=torch.int64, device=dev)
-            his = [datagen.select_threshold(i / 10) for i in range(11)]
-
-            def whole_sweep():  # the metric is the mean over the sweep, so tune on all of it
-                for hi in his:
-                    crys.crys_select(x, n, -(1 << 31), hi, out, cnt, 0)
-            tile = autotune(crys.OP_SELECT, whole_sweep, args)
-            sweep = {}
-            for sigma in [i / 10 for i in range(11)]:
-                hi = datagen.select_threshold(sigma)
-                ms = time_launches(lambda: crys.crys_select(x, n, -(1 << 31), hi, out, cnt, 0),
-                                   args.steps, args.warmup, stream)
-                sweep[f"{sigma:.1f}"] = statistics.median(ms)
-            avg = statistics.mean(sweep.values())
-            alg = statistics.mean([4 * n * (1 + float(s)) for s in sweep])
-            # the independent-threads selection the paper compares against (ablation)
-            stb = crys.crys_select_strawman(None, n, -(1 << 31), 0, None, None, None, -1)
-            stemp = crys.scratch(stb, dev)
-            straw = {}
-            for sigma in (0.0, 0.5, 1.0):
-                hi = datagen.select_threshold(sigma)
-                ms = time_launches(lambda: crys.crys_select_strawman(x, n, -(1 << 31), hi, out, cnt, stemp, stb),
-                                   args.steps, args.warmup, stream)
-                straw[f"{sigma:.1f}"] = round(statistics.median(ms), 4)
-            strawman = {"ms": straw,
-                        "tile_over_independent_at_0.5": round(straw["0.5"] / sweep["0.5"], 2),
-                        "paper": "19 ms independent threads vs 2.1 ms tile-based, V100, 2^29 rows, sigma 0.5 "
-                                 "(Section 3.2)"}
-            line = op_line(args, world, "select", alg / (avg / 1e3) / 1e9, "GB/s", "select_kernel", alg, avg,
-                           {"rows": n, "selectivity": "0.0..1.0 step 0.1 (mean over the sweep)",
-                            "l2": "inputs larger than L2"},
-                           {"sweep_ms": {k: round(v, 4) for k, v in sweep.items()}, "tile": tile,
-                            "independent_threads": strawman})
+            r = op_select(args, dev, stream)
+            line = op_line(args, world, "select", r["GB/s"], "GB/s", "select_kernel", r["alg_bytes_mean"],
+                           r["ms_mean"], {"rows": r["rows"], "selectivity": "0.0..1.0 step 0.1 (mean over the sweep)",
+                                          "l2": "inputs larger than L2"}, {"select": r})
         elif args.workload == "project":
-            n = args.rows or (1 << 29)
-            x1 = dgd.uniform_f32(seed, datagen.STREAMS["proj.x1"], n, dev)
-            x2 = dgd.uniform_f32(seed, datagen.STREAMS["proj.x2"], n, dev)
-            y = torch.empty_like(x1)
-            tile = autotune(crys.OP_PROJECT, lambda: crys.crys_project(x1, x2, n, 2.0, 3.0, crys.PROJ_LINEAR, y), args)
-            res = {}
-            for op, nm in ((crys.PROJ_LINEAR, "linear"), (crys.PROJ_SIGMOID, "sigmoid")):
-                res[nm] = statistics.median(time_launches(
-                    lambda: crys.crys_project(x1, x2, n, 2.0, 3.0, op, y), args.steps, args.warmup, stream))
-            avg = statistics.mean(res.values())
-            line = op_line(args, world, "project", 12 * n / (avg / 1e3) / 1e9, "GB/s", "project_kernel", 12 * n, avg,
-                           {"rows": n, "dtype": "f32", "l2": "inputs larger than L2"},
-                           {"ms": {k: round(v, 4) for k, v in res.items()}, "tile": tile})
+            r = op_project(args, dev, stream)
+            line = op_line(args, world, "project", r["GB/s"], "GB/s", "project_kernel", r["alg_bytes"], r["ms_mean"],
+                           {"rows": r["rows"], "dtype": "f32", "l2": "inputs larger than L2"}, {"project": r})
         elif args.workload == "join":
-            n_probe = args.rows or (1 << 28)
-            fk_pay = None
-            res = {}
-            l2_bytes = int(getattr(torch.cuda.get_device_properties(dev), "L2_cache_size", 126 << 20))
-            for lg in args.join_sizes:
-                nb = 1 << lg
-                bk = dgd.perm_i32(seed, datagen.STREAMS["join.bkey"], nb, dev)
-                bv = dgd.uniform_i32(seed, datagen.STREAMS["join.bval"], nb, 1, 100, dev)
-                ht = crys.HashTable.build(bk, bv)
-                fk = dgd.uniform_i32(seed, datagen.STREAMS["join.fk"], n_probe, 0, nb - 1, dev)
-                pay = dgd.uniform_i32(seed, datagen.STREAMS["join.pay"], n_probe, 1, 100, dev) if fk_pay is None else fk_pay
-                fk_pay = pay
-                s = torch.zeros(2, dtype=torch.int64, device=dev)
-                tile = autotune(crys.OP_PROBE,
-                                lambda: crys.crys_probe_aggregate(fk, pay, n_probe, ht.struct, s[0:1], s[1:2]), args)
-                ms = time_launches(lambda: crys.crys_probe_aggregate(fk, pay, n_probe, ht.struct, s[0:1], s[1:2]),
-                                   args.steps, args.warmup, stream)
-                bms = time_launches(lambda: (crys.crys_hash_init(ht.struct), crys.crys_hash_build(bk, bv, nb, [], ht.struct)),
-                                    max(1, args.steps // 2), 1, stream)
-                pm = statistics.median(ms)
-                # Section 4.3 model: the probe scan plus one 32-byte sector per probe that
-                # misses L2 (hit share pi = L2 size / table size, at most 1)
-                pi = min(1.0, l2_bytes / ht.nbytes)
-                model = 8 * n_probe + (1.0 - pi) * n_probe * 32
-                res[f"2^{lg}"] = {"probe_ms": round(pm, 4), "build_ms": round(statistics.median(bms), 4),
-                                  "table_mb": round(ht.nbytes / 2 ** 20, 3), "tile": tile,
-                                  "model_bytes": int(model),
-                                  "model_frac": round(model / (pm / 1e3) / 1e9 / measured_hbm_peak()[0], 4)}
-                del ht, bk, bv, fk
-            # partial matches on the largest table: probe keys spread over [0, N / pi), so a
-            # share pi of them finds its key (the others read a slot and miss)
-            partial = {}
-            lg = args.join_sizes[-1]
-            nb = 1 << lg
-            bk = dgd.perm_i32(seed, datagen.STREAMS["join.bkey"], nb, dev)
-            bv = dgd.uniform_i32(seed, datagen.STREAMS["join.bval"], nb, 1, 100, dev)
-            ht = crys.HashTable.build(bk, bv)
-            for pi in (0.5, 0.1):
-                fk = dgd.uniform_i32(seed, datagen.STREAMS["join.fk"], n_probe, 0, int(nb / pi) - 1, dev)
-                s = torch.zeros(2, dtype=torch.int64, device=dev)
-                ms = time_launches(lambda: crys.crys_probe_aggregate(fk, fk_pay, n_probe, ht.struct, s[0:1], s[1:2]),
-                                   args.steps, args.warmup, stream)
-                partial[f"{pi}"] = {"probe_ms": round(statistics.median(ms), 4),
-                                    "matched": round(int(s[1].item()) / n_probe, 4)}
-                del fk
-            del ht, bk, bv
-            # headline: the largest table (HBM-resident probes), against the model's bytes
-            last = res[f"2^{args.join_sizes[-1]}"]
-            alg = last["model_bytes"]
-            line = op_line(args, world, "join", alg / (last["probe_ms"] / 1e3) / 1e9, "GB/s", "probe_kernel", alg,
-                           last["probe_ms"], {"probe_rows": n_probe, "build_rows": f"2^{args.join_sizes[0]}..2^{args.join_sizes[-1]}",
-                                              "fill": "50%", "l2": "probe side larger than L2"},
-                           {"sweep": res, "l2_bytes": l2_bytes, "partial_match_largest_table": partial,
-                            "note": "algorithmic bytes = probe scan 8|P| + (1 - pi)|P| 32-byte slot sectors, "
-                                    "pi = min(1, L2 / table) (Section 4.3 model)"})
+            r = op_join(args, dev, stream, args.join_sizes)
+            last = r["sweep"][f"2^{args.join_sizes[-1]}"]
+            line = op_line(args, world, "join", gbs(last["model_bytes"], last["probe_ms"]), "GB/s", "probe_kernel",
+                           last["model_bytes"], last["probe_ms"],
+                           {"probe_rows": r["probe_rows"], "build_rows": f"2^{args.join_sizes[0]}..2^{args.join_sizes[-1]}",
+                            "fill": "50%", "l2": "probe side larger than L2"}, {"join": r})
         elif args.workload == "sort":
-            n = args.rows or (1 << 28)
-            keys = dgd.bits_i32(seed, datagen.STREAMS["sort.key"], n, dev)
-            vals = torch.arange(n, dtype=torch.int32, device=dev)
-            ko, vo = torch.empty_like(keys), torch.empty_like(vals)
-            tb = crys.crys_sort(None, None, None, None, n, None, -1)
-            temp = crys.scratch(tb, dev)
-            tile = autotune(crys.OP_SORT, lambda: crys.crys_sort(keys, vals, ko, vo, n, temp, tb), args)
-            ms = time_launches(lambda: crys.crys_sort(keys, vals, ko, vo, n, temp, tb), args.steps, args.warmup, stream)
-            avg = statistics.median(ms)
-            line = op_line(args, world, "sort", n / (avg / 1e3) / 1e6, "Mkeys/s", "sort_pass_kernel", 68 * n, avg,
-                           {"rows": n, "l2": "inputs larger than L2", "passes": "4 x 8-bit, stable"},
-                           {"tile": tile})
+            r = op_sort(args, dev, stream)
+            s = r["lsd_stable"]
+            line = op_line(args, world, "sort", s["Mkeys/s"], "Mkeys/s", "sort_pass_kernel", 68 * r["rows"], s["ms"],
+                           {"rows": r["rows"], "l2": "inputs larger than L2", "passes": "4 x 8-bit, stable"},
+                           {"sort": r})
         elif args.workload == "q1":
             sizes = [args.rows] if args.rows else [1 << 22, 1 << 28]
-            results, tiles, graphed = {}, {}, {}
-            flush_buf = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
-            for n in sizes:
-                t = dgd.q1_tables(seed, n, dev)
-                f, d = t["fact"], t["dim"]
-                ht = crys.HashTable.build(d["key"], d["yr"], filters=[(d["yr"], 3, 3)])
-                sums = torch.zeros(1, dtype=torch.int64, device=dev)
-                cnts = torch.zeros(1, dtype=torch.int64, device=dev)
-                table = crys.make_table([f["fk"], f["a"], f["b"], f["c"]])
-                plan = crys.make_plan([(1, -(1 << 31), 24), (2, 1, 3)], [(0, ht, 0)], ("mul", 3, 2), sums, cnts)
-                tile = autotune(crys.OP_PLAN, lambda: (l2_flush(flush_buf), crys.crys_run_plan(table, plan)), args)
-                ms = time_launches(lambda: crys.crys_run_plan(table, plan), args.steps, args.warmup, stream,
-                                   flush=lambda: l2_flush(flush_buf))
-                results[n] = statistics.median(ms)
-                tiles[n] = tile
-                graphed[n] = graph_differential_ms(lambda: crys.crys_run_plan(table, plan),
-                                                   lambda: l2_flush(flush_buf))
-                del t, f, d, ht, table, plan
+            r = op_q1(args, dev, stream, sizes)
             n = sizes[0]
-            avg = results[n]
-            peak_gbs = measured_hbm_peak()[0]
-            extra = {"by_rows": {str(k): {"ms": round(v, 4), "GB/s": round(16 * k / (v / 1e3) / 1e9, 1),
-                                          "frac": round(16 * k / (v / 1e3) / 1e9 / peak_gbs, 4),
-                                          "graph_ms": round(graphed[k], 4),
-                                          "graph_frac": round(16 * k / (graphed[k] / 1e3) / 1e9 / peak_gbs, 4)
-                                          if graphed[k] > 0 else None,
-                                          "tile": tiles[k]}
-                                 for k, v in results.items()},
-                     "graph_ms_note": "per-launch device time from CUDA-graph replays of k x {L2 flush, "
-                                      "kernel} minus k x {L2 flush}: no launch or event overhead"}
-            line = op_line(args, world, "q1", 16 * n / (avg / 1e3) / 1e9, "GB/s", "plan_kernel", 16 * n, avg,
+            q = r["by_rows"][str(n)]
+            line = op_line(args, world, "q1", q["GB/s"], "GB/s", "plan_kernel", 16 * n, q["ms"],
                            {"rows": n, "dtype": "int64", "l2": "flushed between timed launches (512 MB write)",
                             "query": "yr == 3 AND a < 25 AND 1 <= b <= 3, SUM(c * b), 2556-row date-like dimension"},
-                           extra)
+                           {"q1": r})
         else:
             raise SystemExit(f"unknown workload {args.workload}")
     line["gpu_launches"] = int(crys.crys_launch_count() - launches0)
@@ -690,41 +800,40 @@ def run_operator(args, rank, world, local):
 # ----------------------------------------------------------------------------- reference arm
 
 def run_reference(args, rank, world):
-    """The oracle as it stands, on the host cores, on a bounded sample of each step's
-    workload (a few of the step's queries, each timed over 0 and over the first
-    `cpu_sample_rows` fact rows and extrapolated to the full table), reported in our
-    arm's unit."""
+    """The oracle as it stands, on the host cores, as the reference arm: every step runs
+    `ref_queries` queries of the step's batch over ALL fact rows (wall time per step is
+    the measured duration), reported in our arm's unit and config."""
     if rank != 0:
         return None
-    import datagen
     import oracle
     oracle.build()
     threads = oracle.hardware_threads()
     if args.workload != "served":
         raise SystemExit("--impl reference is implemented for the served workload")
-    rows = min(args.cpu_sample_rows, args.rows)
-    host = datagen.ss_tables(args.seed, rows, dim_scale=args.dim_scale)
-    full_s, spent, nq = 0.0, 0.0, 0
+    t0 = time.perf_counter()
+    host = host_star_schema(args.seed, args.rows, args.dim_scale, threads)
+    gen_s = time.perf_counter() - t0
+    step_s = []
     for s in range(args.warmup + args.steps):
-        qs = batch_queries(args.seed, s)[: args.cpu_queries]
+        qs = batch_queries(args.seed, s)[: args.ref_queries]
+        t0 = time.perf_counter()
         for q in qs:
-            f, sp = oracle_query_seconds(host, q, rows, args.rows, threads)
-            if s >= args.warmup:
-                full_s += f
-                spent += sp
-                nq += 1
-    qps = nq / full_s
+            oracle.ss_run(host, q, threads=threads)
+        if s >= args.warmup:
+            step_s.append(time.perf_counter() - t0)
+    total = sum(step_s)
+    nq = args.ref_queries * args.steps
+    qps = nq / total
     return {"metric": METRIC, "value": round(qps, 4), "unit": "queries/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(full_s / args.steps * 1e3, 3),
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total / args.steps * 1e3, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
             "data": "synthetic (seeded counter-based generator)", "impl": "reference",
-            "config": {"workload": "served star-schema stream: fact 600M rows x 8 int32 cols, dims "
-                                   "2556/200K/3M/1.4M rows, seeded select-join-group-by queries",
-                       "fact_rows": args.rows, "batch_queries": BATCH},
+            "config": served_config(args, world),
             "cpu_baseline": {"value": round(qps, 4), "unit": "queries/s", "cores": threads, "kind": "oracle",
-                             "sample": f"each step: {args.cpu_queries} of the step's queries, each timed over 0 "
-                                       f"and over the first {rows} fact rows, extrapolated to {args.rows} rows "
-                                       f"({spent:.1f} s spent in timed steps)"},
+                             "sample": f"each step: {args.ref_queries} of the step's {BATCH} queries, timed over "
+                                       f"all {args.rows} fact rows (a step is a fraction of a batch: the oracle "
+                                       f"takes seconds per query); inputs generated on the host in {gen_s:.1f} s "
+                                       "before the timed steps"},
             "e2e": {"value": round(qps, 4), "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -744,11 +853,12 @@ def main():
     p.add_argument("--segments", type=int, default=8)
     p.add_argument("--batch", type=int, default=BATCH, help="queries per shared scan (1..32)")
     p.add_argument("--served-queries", type=int, default=512)
-    p.add_argument("--cpu-sample-rows", type=int, default=2_000_000)
-    p.add_argument("--cpu-queries", type=int, default=4, help="queries per step timed on the CPU")
+    p.add_argument("--cpu-queries", type=int, default=2, help="queries timed on the CPU for cpu_baseline")
+    p.add_argument("--ref-queries", type=int, default=1, help="queries per step of the reference arm")
     p.add_argument("--join-sizes", type=int, nargs="+", default=[10, 14, 18, 20, 22, 24, 26, 27])
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--quick", action="store_true", help="skip the one-at-a-time and served-loop legs")
+    p.add_argument("--quick", action="store_true", help="skip the one-at-a-time, served-loop and operator legs")
+    p.add_argument("--no-operators", action="store_true", help="skip the operators block (configs 1-4)")
     p.add_argument("--no-tune", action="store_true", help="keep the default tile shapes")
     args = p.parse_args()
     if args.warmup < 3:

@@ -54,6 +54,9 @@ class ServeStats:
     deferred: int = 0
     max_active: int = 0
     replays: int = 0                      # launches that were CUDA graph replays
+    h2d_bytes: int = 0                    # argument blocks copied from pinned host memory
+    d2h_bytes: int = 0                    # results copied to pinned host memory
+    peak_held_bytes: int = 0              # largest footprint of admitted + finishing queries
     latencies_s: list = field(default_factory=list)
 
     @property
@@ -80,11 +83,15 @@ class QueryServer:
         step = (step + 4095) // 4096 * 4096           # segment starts stay 16-byte aligned
         self.bounds = [(b, min(n, b + step)) for b in range(0, n, step)] or [(0, 0)]
         self.next_segment = 0
+        self.h2d_bytes = 0
         self.replay = ReplayedScan(store, self.stream) if graphs and mode == "resident" else None
 
     # -- admission ----------------------------------------------------------------------
-    def fits(self, req: Request, active: list) -> bool:
-        used = sum(r.mem for r in active)
+    def fits(self, req: Request, active: list, finishing: tuple = ()) -> bool:
+        """A free slot, and memory for `req` next to the active queries and the finishing
+        ones whose last launch is still on the GPU (they hold their tables and outputs
+        until that launch has been harvested)."""
+        used = sum(r.mem for r in active) + sum(r.mem for r in finishing)
         return len(active) < self.max_slots and used + req.mem <= self.memory_budget
 
     def _admit(self, req: Request, now: float) -> None:
@@ -99,7 +106,9 @@ class QueryServer:
         b, e = self.bounds[self.next_segment]
         cqs = [r.compiled for r in active]
         fresh = [i for i, r in enumerate(active) if r.seen == 0]
-        if self.replay is None or not self.replay.launch(cqs, b, e, fresh):
+        if self.replay is not None and self.replay.launch(cqs, b, e, fresh):
+            self.h2d_bytes += self.replay.block_bytes
+        else:
             with torch.cuda.stream(self.stream):
                 if self.replay is not None:          # outputs were left for the replay to clear
                     for i in fresh:
@@ -134,15 +143,16 @@ class QueryServer:
         active: list = []
         stats = ServeStats()
         nseg = len(self.bounds)
-        torch.cuda.synchronize(self.store.device)
+        self._sync()
         replays0 = self.replay.replays if self.replay is not None else 0
+        self.h2d_bytes = 0
         t0 = time.perf_counter()
         inflight = None   # (event, finishing requests) of the launch on the GPU
         while pi < len(pending) or active or inflight:
             now = time.perf_counter() - t0
             while pi < len(pending) and reqs[pending[pi]].arrival_s <= now:
                 r = reqs[pending[pi]]
-                if not self.fits(r, active):
+                if not self.fits(r, active, inflight[1] if inflight else ()):
                     if not r.deferred:           # waits for a slot or memory to free up
                         r.deferred = True
                         stats.deferred += 1
@@ -151,23 +161,18 @@ class QueryServer:
                 active.append(r)
                 pi += 1
             stats.max_active = max(stats.max_active, len(active))
+            held = sum(r.mem for r in active) + (sum(r.mem for r in inflight[1]) if inflight else 0)
+            stats.peak_held_bytes = max(stats.peak_held_bytes, held)
             if active:
                 self._launch(active)
                 stats.launches += 1
                 finishing = [r for r in active if r.seen >= nseg]
                 active = [r for r in active if r.seen < nseg]
                 for r in finishing:
-                    sums = torch.empty(r.compiled.groups, dtype=torch.int64, pin_memory=True)
-                    counts = torch.empty(r.compiled.groups, dtype=torch.int64, pin_memory=True)
-                    with torch.cuda.stream(self.stream):
-                        sums.copy_(r.compiled.sums, non_blocking=True)
-                        counts.copy_(r.compiled.counts, non_blocking=True)
-                    r.result = (sums, counts)
+                    stats.d2h_bytes += self._copy_out(r)
                 if inflight is not None:
                     self._harvest(inflight, t0, stats)
-                ev2 = torch.cuda.Event()
-                ev2.record(self.stream)
-                inflight = (ev2, finishing)
+                inflight = (self._record(), finishing)
             else:
                 if inflight is not None:
                     self._harvest(inflight, t0, stats)
@@ -179,8 +184,32 @@ class QueryServer:
                         time.sleep(min(wait, 0.001))
         stats.wall_s = time.perf_counter() - t0
         stats.replays = (self.replay.replays - replays0) if self.replay is not None else 0
-        check_device_errors(self.stream)
+        stats.h2d_bytes = self.h2d_bytes
+        self._check()
         return reqs, stats
+
+    # -- device plumbing (one place, so that the admission logic runs without a GPU) --------
+    def _sync(self) -> None:
+        torch.cuda.synchronize(self.store.device)
+
+    def _record(self):
+        ev = torch.cuda.Event()
+        ev.record(self.stream)
+        return ev
+
+    def _check(self) -> None:
+        check_device_errors(self.stream)
+
+    def _copy_out(self, r: Request) -> int:
+        """Queues the copy of a finished query's sums and counts to pinned host memory on
+        the serving stream; returns the bytes copied."""
+        sums = torch.empty(r.compiled.groups, dtype=torch.int64, pin_memory=True)
+        counts = torch.empty(r.compiled.groups, dtype=torch.int64, pin_memory=True)
+        with torch.cuda.stream(self.stream):
+            sums.copy_(r.compiled.sums, non_blocking=True)
+            counts.copy_(r.compiled.counts, non_blocking=True)
+        r.result = (sums, counts)
+        return sums.numel() * sums.element_size() + counts.numel() * counts.element_size()
 
     def _harvest(self, inflight, t0, stats: ServeStats) -> None:
         ev, finishing = inflight

@@ -35,9 +35,19 @@ from . import (HashTable, crys_get_tile, crys_hash_build, crys_hash_init, crys_p
 
 @dataclass
 class Schema:
-    """Names and domains of the fact columns and of each dimension's attributes."""
+    """Names and domains of the fact columns and of each dimension's attributes.
+
+    The package knows no particular workload: whoever loads a star schema states its
+    column names, each dimension's foreign-key column and attribute cardinalities (the
+    dictionary-encoded domains of Section 5.2), e.g. ``Schema.from_spec(cols, dims)``."""
     fact_cols: list
     dims: dict          # dim -> {"fk": fact col name, "attrs": {attr: cardinality}}
+
+    @classmethod
+    def from_spec(cls, fact_cols, dims: dict) -> "Schema":
+        """From a column list and a {dim: {"fk": col, "attrs": {attr: card}, ...}} mapping
+        (other keys of a dimension's entry are ignored)."""
+        return cls(list(fact_cols), {d: {"fk": s["fk"], "attrs": dict(s["attrs"])} for d, s in dims.items()})
 
 
 @dataclass
@@ -179,7 +189,13 @@ class ResidentStarSchema:
         crys_run_plan(self.table, cq.plan, stream)
 
     def scratch(self, need: int) -> torch.Tensor:
+        """The query-bitmap scratch, grown when a batch needs more.  Earlier launches on
+        any stream may still read or write the old block, so the device is drained before
+        it goes back to the allocator (growth is rare: the store is built with room for
+        every resident table)."""
         if self._scratch.numel() < need:
+            torch.cuda.synchronize(self.device)
+            self._scratch = None
             self._scratch = torch.empty(need, dtype=torch.uint8, device=self.device)
         return self._scratch
 
@@ -210,12 +226,6 @@ class ResidentStarSchema:
         return 4 * self.n_rows * len(self.query_columns(query))
 
 
-def served_schema() -> Schema:
-    import datagen
-    return Schema(list(datagen.SS_FACT_COLS),
-                  {d: {"fk": s["fk"], "attrs": dict(s["attrs"])} for d, s in datagen.SS_DIMS.items()})
-
-
 class ReplayedScan:
     """Tagged shared scans of a serving loop through captured CUDA graphs.
 
@@ -228,6 +238,7 @@ class ReplayedScan:
         self.store = store
         self.stream = stream
         nb = crys_tagged_block_bytes()
+        self.block_bytes = nb                # bytes copied host -> device per launch
         self.dev_block = torch.empty(nb, dtype=torch.uint8, device=store.device)
         self.host = [torch.empty(nb, dtype=torch.uint8, pin_memory=True) for _ in range(2)]
         self.graphs = [None, None]

@@ -91,11 +91,13 @@ def test_generator_library_exports(crys):
 
 
 def test_product_does_not_import_oracle():
+    """The package imports neither the oracle nor the input generator (it owns no workload)."""
     import subprocess
     import sys
     code = ("import sys; sys.path.insert(0, %r); import paper_2003_01178_gb300, "
             "paper_2003_01178_gb300.starschema, paper_2003_01178_gb300.server; "
-            "assert 'oracle' not in sys.modules, 'oracle imported'" % ROOT)
+            "assert 'oracle' not in sys.modules, 'oracle imported'; "
+            "assert 'datagen' not in sys.modules, 'the input generator imported'" % ROOT)
     subprocess.check_call([sys.executable, "-c", code])
 
 

@@ -65,9 +65,9 @@ def _schema_tables(seed, n, scale):
 
 @pytest.fixture(scope="module")
 def star(crys):
-    from paper_2003_01178_gb300.starschema import ResidentStarSchema, served_schema
+    from paper_2003_01178_gb300.starschema import ResidentStarSchema, Schema
     host, fact, dims = _schema_tables(5, 300_007, 0.02)
-    return host, ResidentStarSchema(served_schema(), fact, dims)
+    return host, ResidentStarSchema(Schema.from_spec(datagen.SS_FACT_COLS, datagen.SS_DIMS), fact, dims)
 
 
 def _check(orc, host, cq, query):

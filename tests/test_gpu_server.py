@@ -15,11 +15,11 @@ def store():
         pytest.skip("no GPU")
     from paper_2003_01178_gb300 import _build
     _build.build()
-    from paper_2003_01178_gb300.starschema import ResidentStarSchema, served_schema
+    from paper_2003_01178_gb300.starschema import ResidentStarSchema, Schema
     host = datagen.ss_tables(3, 500_009, dim_scale=0.02)
     fact = {k: torch.from_numpy(v).cuda() for k, v in host["fact"].items()}
     dims = {d: {k: torch.from_numpy(v).cuda() for k, v in t.items()} for d, t in host["dims"].items()}
-    return host, ResidentStarSchema(served_schema(), fact, dims)
+    return host, ResidentStarSchema(Schema.from_spec(datagen.SS_FACT_COLS, datagen.SS_DIMS), fact, dims)
 
 
 @pytest.mark.parametrize("graphs", [True, False])

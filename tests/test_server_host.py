@@ -1,5 +1,6 @@
 """Host-side logic of the serving loop (no GPU): admission by slots and memory, requests
 that can never fit, segment bounds of the circular scan."""
+import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
@@ -57,3 +58,61 @@ def test_segments_cover_rows_once_and_stay_aligned():
         for (a, b), (c, _) in zip(s.bounds, s.bounds[1:]):
             assert b == c and a % 4096 == 0
         assert len(s.bounds) <= 8
+
+
+class _Event:
+    def synchronize(self):
+        pass
+
+
+class _HostServer(QueryServer):
+    """The serving loop with its device steps replaced by host bookkeeping: each launch
+    checks that the queries still holding memory (admitted and not yet harvested) fit the
+    budget."""
+
+    def __init__(self, store, budget, max_slots, segments):
+        srv = _server(store, budget=budget, max_slots=max_slots, segments=segments)
+        self.__dict__.update(srv.__dict__)
+        self.replay = None
+        self.h2d_bytes = 0
+        self.requests = []
+        self.worst = 0
+
+    def _sync(self):
+        pass
+
+    def _record(self):
+        return _Event()
+
+    def _check(self):
+        pass
+
+    def _admit(self, req, now):
+        req.compiled = type("C", (), {"groups": 1})()
+        req.admitted_s = now
+        req.seen = 0
+        self.requests.append(req)
+
+    def _launch(self, active):
+        held = sum(r.mem for r in self.requests if r.compiled is not None)
+        self.worst = max(self.worst, held)
+        for r in active:
+            r.seen += 1
+        self.next_segment = (self.next_segment + 1) % len(self.bounds)
+
+    def _copy_out(self, r):
+        r.result = (torch.zeros(1, dtype=torch.int64), torch.zeros(1, dtype=torch.int64))
+        return 16
+
+
+def test_finishing_queries_count_against_the_budget_until_harvested():
+    # 12 queries of 300..700 bytes under a 1000-byte budget, all queued at t=0: a query
+    # that finishes in a launch keeps its memory until that launch has been harvested,
+    # so the next admission must not count on it
+    need = {i: 300 + 100 * (i % 5) for i in range(12)}
+    srv = _HostServer(FakeStore(1 << 16, need), budget=1000, max_slots=4, segments=3)
+    reqs, stats = srv.serve([{"id": i} for i in range(12)], np.zeros(12), realtime=False)
+    assert stats.completed == 12 and all(r.result is not None for r in reqs)
+    assert srv.worst <= 1000, srv.worst
+    assert stats.peak_held_bytes <= 1000
+    assert stats.d2h_bytes == 16 * 12

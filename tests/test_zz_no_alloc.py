@@ -69,3 +69,18 @@ def test_static_select_limits(crys):
     x = torch.arange(1 << 25, dtype=torch.int32, device="cuda")      # exactly the maximum
     got = _static(crys, x, 100, 1 << 24)
     assert np.array_equal(got, np.arange(100, (1 << 24) + 1, dtype=np.int32))
+
+
+def test_static_select_empty_inputs_then_a_normal_call(crys):
+    # n = 0 and an empty range (lo > hi) return no rows; the empty range clears the static
+    # array's used part, and the next call on the array is still exact
+    empty = torch.empty(0, dtype=torch.int32, device="cuda")
+    assert _static(crys, empty, 0, 10).size == 0
+    x = torch.from_numpy(datagen.uniform_i32(61, datagen.STREAMS["sel.x"], 100_003, 0, I32_MAX)).cuda()
+    assert _static(crys, x, 10, 5).size == 0
+    hi = datagen.select_threshold(0.4)
+    assert np.array_equal(_static(crys, x, I32_MIN, hi), _regular(crys, x, I32_MIN, hi))
+
+
+def test_static_select_left_no_device_error(crys):
+    assert crys.crys_device_errors(clear=True) == 0
