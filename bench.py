@@ -531,13 +531,12 @@ def time_launches(fn, steps, warmup, stream, flush=None):
     return ms
 
 
-def op_select(args, dev, stream, strawman=True):
+def op_select(args, dev, stream, n=1 << 29, strawman=True):
     """Config 2(1): selection of 2^29 int32 uniform in [0, 2^31), x < v, sigma 0..1."""
     import torch
     import datagen
     import datagen.device as dgd
     import paper_2003_01178_gb300 as crys
-    n = args.rows or (1 << 29)
     x = dgd.uniform_i32(args.seed, datagen.STREAMS["sel.x"], n, 0, (1 << 31) - 1, dev)
     out = torch.empty(n, dtype=torch.int32, device=dev)
     cnt = torch.zeros(1, dtype=torch.int64, device=dev)
@@ -576,13 +575,12 @@ def op_select(args, dev, stream, strawman=True):
     return res
 
 
-def op_project(args, dev, stream):
+def op_project(args, dev, stream, n=1 << 29):
     """Config 2(2): y = 2 x1 + 3 x2 and its sigmoid over 2^29 float32 rows."""
     import torch
     import datagen
     import datagen.device as dgd
     import paper_2003_01178_gb300 as crys
-    n = args.rows or (1 << 29)
     x1 = dgd.uniform_f32(args.seed, datagen.STREAMS["proj.x1"], n, dev)
     x2 = dgd.uniform_f32(args.seed, datagen.STREAMS["proj.x2"], n, dev)
     y = torch.empty_like(x1)
@@ -631,13 +629,12 @@ def op_q1(args, dev, stream, sizes):
                              "k x {L2 flush}: no launch or event overhead"}
 
 
-def op_sort(args, dev, stream):
+def op_sort(args, dev, stream, n=1 << 28):
     """Config 4: radix sort of 2^28 (key, row id) pairs."""
     import torch
     import datagen
     import datagen.device as dgd
     import paper_2003_01178_gb300 as crys
-    n = args.rows or (1 << 28)
     keys = dgd.bits_i32(args.seed, datagen.STREAMS["sort.key"], n, dev)
     vals = torch.arange(n, dtype=torch.int32, device=dev)
     ko, vo = torch.empty_like(keys), torch.empty_like(vals)
@@ -651,17 +648,27 @@ def op_sort(args, dev, stream):
         "frac": frac(68 * n, ms), "tile": tile,
         "bytes": "one 4N key read for all digit histograms + 4 passes x (8N read + 8N written) = 68N"},
         "paper": "V100: 27.08 ms for 2^28 key+value pairs, unstable MSB sort (Section 4.4)"}
+    del temp
+    # the paper's own GPU sort: most-significant-digit first, unstable
+    tb = crys.crys_sort_msb(None, None, None, None, n, None, -1)
+    temp = crys.scratch(tb, dev)
+    ms = statistics.median(time_launches(lambda: crys.crys_sort_msb(keys, vals, ko, vo, n, temp, tb),
+                                         args.steps, args.warmup, stream))
+    res["msb_unstable"] = {
+        "ms": round(ms, 4), "Mkeys/s": round(n / (ms / 1e3) / 1e6, 1), "GB/s": round(gbs(56 * n, ms), 1),
+        "frac": frac(56 * n, ms), "over_lsd": round(res["lsd_stable"]["ms"] / ms, 3),
+        "bytes": "2 partition passes x (4N histogram read + 8N read + 8N written) + local sort of every "
+                 "16-bit bucket (8N read + 8N written) = 56N"}
     del keys, vals, ko, vo, temp
     return res
 
 
-def op_join(args, dev, stream, sizes, partial=True):
+def op_join(args, dev, stream, sizes, n_probe=1 << 28, partial=True):
     """Config 3: build N unique keys at 50% fill, probe 2^28 foreign keys, SUM(payload * value)."""
     import torch
     import datagen
     import datagen.device as dgd
     import paper_2003_01178_gb300 as crys
-    n_probe = args.rows or (1 << 28)
     res = {}
     l2_bytes = int(getattr(torch.cuda.get_device_properties(dev), "L2_cache_size", 126 << 20))
     pay = dgd.uniform_i32(args.seed, datagen.STREAMS["join.pay"], n_probe, 1, 100, dev)
@@ -691,7 +698,27 @@ def op_join(args, dev, stream, sizes, partial=True):
                           "table_mb": round(ht.nbytes / 2 ** 20, 3), "tile": tile,
                           "model_bytes": int(model32), "model_frac": frac(model32, pm),
                           "model_bytes_128B_lines": int(model128), "model_frac_128B_lines": frac(model128, pm)}
-        del ht, bk, bv, fk
+        del ht
+        if lg >= args.partition_from:
+            # the radix-partitioned join on the same inputs (build and probe included)
+            jtb = crys.crys_join_partitioned(None, None, nb, None, None, n_probe, None, None, None, -1)
+            jtemp = crys.scratch(jtb, dev)
+            jm = statistics.median(time_launches(
+                lambda: crys.crys_join_partitioned(bk, bv, nb, fk, pay, n_probe, s[0:1], s[1:2], jtemp, jtb),
+                args.steps, args.warmup, stream))
+            bits = 0
+            while bits < 16 and (nb >> bits) > 2048:
+                bits += 1
+            passes = 0 if bits == 0 else (1 if bits == 1 else 2)
+            jbytes = passes * 20 * (nb + n_probe) + 8 * (nb + n_probe)
+            res[f"2^{lg}"]["partitioned"] = {
+                "ms": round(jm, 4), "over_build_plus_probe": round((pm + bms) / jm, 3),
+                "over_probe_alone": round(pm / jm, 3), "hash_bits": bits, "passes": passes,
+                "GB/s": round(gbs(jbytes, jm), 1), "frac": frac(jbytes, jm),
+                "bytes": "per partition pass 20 B per row of each side (4 B histogram read, 8 B read, 8 B "
+                         "written), then 8 B per row of each side read by the per-partition build and probe"}
+            del jtemp
+        del bk, bv, fk
     out = {"kernel": "probe_kernel", "probe_rows": n_probe, "fill": "50%", "sweep": res, "l2_bytes": l2_bytes,
            "note": "model bytes = probe scan 8|P| + (1 - pi)|P| x line, pi = min(1, L2 / table) (Section 4.3 "
                    "model); line = 32 B (sector) or 128 B (the line a random miss fills on this GPU)"}
@@ -760,23 +787,23 @@ def run_operator(args, rank, world, local):
     launches0 = crys.crys_launch_count()
     with ClockSampler(local) as clocks:
         if args.workload == "select":
-            r = op_select(args, dev, stream)
+            r = op_select(args, dev, stream, args.rows or (1 << 29))
             line = op_line(args, world, "select", r["GB/s"], "GB/s", "select_kernel", r["alg_bytes_mean"],
                            r["ms_mean"], {"rows": r["rows"], "selectivity": "0.0..1.0 step 0.1 (mean over the sweep)",
                                           "l2": "inputs larger than L2"}, {"select": r})
         elif args.workload == "project":
-            r = op_project(args, dev, stream)
+            r = op_project(args, dev, stream, args.rows or (1 << 29))
             line = op_line(args, world, "project", r["GB/s"], "GB/s", "project_kernel", r["alg_bytes"], r["ms_mean"],
                            {"rows": r["rows"], "dtype": "f32", "l2": "inputs larger than L2"}, {"project": r})
         elif args.workload == "join":
-            r = op_join(args, dev, stream, args.join_sizes)
+            r = op_join(args, dev, stream, args.join_sizes, args.rows or (1 << 28))
             last = r["sweep"][f"2^{args.join_sizes[-1]}"]
             line = op_line(args, world, "join", gbs(last["model_bytes"], last["probe_ms"]), "GB/s", "probe_kernel",
                            last["model_bytes"], last["probe_ms"],
                            {"probe_rows": r["probe_rows"], "build_rows": f"2^{args.join_sizes[0]}..2^{args.join_sizes[-1]}",
                             "fill": "50%", "l2": "probe side larger than L2"}, {"join": r})
         elif args.workload == "sort":
-            r = op_sort(args, dev, stream)
+            r = op_sort(args, dev, stream, args.rows or (1 << 28))
             s = r["lsd_stable"]
             line = op_line(args, world, "sort", s["Mkeys/s"], "Mkeys/s", "sort_pass_kernel", 68 * r["rows"], s["ms"],
                            {"rows": r["rows"], "l2": "inputs larger than L2", "passes": "4 x 8-bit, stable"},
@@ -856,6 +883,8 @@ def main():
     p.add_argument("--cpu-queries", type=int, default=2, help="queries timed on the CPU for cpu_baseline")
     p.add_argument("--ref-queries", type=int, default=1, help="queries per step of the reference arm")
     p.add_argument("--join-sizes", type=int, nargs="+", default=[10, 14, 18, 20, 22, 24, 26, 27])
+    p.add_argument("--partition-from", type=int, default=20,
+                   help="time the radix-partitioned join for build sides of at least 2^k rows")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--quick", action="store_true", help="skip the one-at-a-time, served-loop and operator legs")
     p.add_argument("--no-operators", action="store_true", help="skip the operators block (configs 1-4)")

@@ -63,6 +63,19 @@ int crys_device_errors(int32_t* flags, int clear, crys_stream s);
 /* Total number of kernels this library has launched in this process (all devices). */
 int64_t crys_launch_count(void);
 
+/* Test hook for the bounded waits (failure detection; the paper has no counterpart).
+ * The NEXT call of `op` in this process - an order-preserving crys_select (also through
+ * crys_select_static) or a crys_sort - hands out tile ids starting at `first_tile`
+ * instead of 0 and bounds its look-back waits by `wait_limit_ns` (1 us .. 2 s) instead
+ * of 2 s.  With first_tile > 0 the tiles before it never publish their counts, so the
+ * tile after them waits for a flag that nothing sets: the call's blocks give up once
+ * the bound has passed, CRYS_DEV_TIMEOUT is set in the device error word and the call's
+ * outputs are incomplete; nothing hangs and nothing traps.  A call that gives up marks
+ * only its own scratch (the per-call abort word), so later calls run normally whether or
+ * not the error word was cleared.  One-shot: the request is consumed by that call.
+ * CRYS_EINVAL for another op, a negative tile or a bound outside the range. */
+int crys_debug_stall(int op, int32_t first_tile, int64_t wait_limit_ns);
+
 /* ------------------------------------------------------------------ selection
  * Section 3.2 (query Q0, Figure "tile-example") and Section 4.2 (query Q3):
  * SELECT x FROM R WHERE lo <= x <= hi, as one kernel: each thread block loads a tile,
@@ -183,6 +196,38 @@ int crys_probe_aggregate(const int32_t* fk, const int32_t* payload, int64_t n,
  * keys_out/vals_out must not overlap the inputs; the inputs are not modified. */
 int crys_sort(const int32_t* keys_in, const int32_t* vals_in, int32_t* keys_out,
               int32_t* vals_out, int64_t n, void* d_temp, size_t* temp_bytes, crys_stream s);
+
+/* Most-significant-digit radix sort (Section 4.4: the GPU sort behind the paper's sort
+ * figure is an MSB radix sort, not stable).  Two 8-bit partition passes on the top two
+ * digits (signed order: the sign bit is flipped), each a histogram, a scan and a scatter
+ * whose tiles rank their keys with shared-memory atomics and reserve each digit's run with
+ * one global atomic; then every bucket of the top 16 bits is sorted inside one thread
+ * block by the low 16 bits (4 stable passes of 4 bits in shared memory) and stored.
+ * Keys come out in ascending signed order; rows with EQUAL keys may come out in any order
+ * (unstable), so (key, value) pairs are a permutation of the input pairs.  A bucket of
+ * more than 8192 rows (heavily repeated top bits) is sorted by one block through global
+ * memory: correct for every input, slow only for such skew.  n <= 2^31 - 1; keys_out /
+ * vals_out must not overlap the inputs.  Scratch (two-call size query): n keys + n values
+ * plus about 1.3 MB of bucket arrays. */
+int crys_sort_msb(const int32_t* keys_in, const int32_t* vals_in, int32_t* keys_out,
+                  int32_t* vals_out, int64_t n, void* d_temp, size_t* temp_bytes, crys_stream s);
+
+/* Radix-partitioned hash join with aggregation (Section 4.3 names partitioned joins as the
+ * alternative to the no-partitioning join when the build side is far beyond the caches).
+ * Build side (bkeys[i], bvals[i]), nb rows, unique keys; probe side (fk[j], payload[j]), np
+ * rows.  Both sides are partitioned in up to two passes by the top bits of the
+ * multiplicative hash key * 2654435769 (bits chosen so that a build partition averages at
+ * most 2048 rows), then each probe tile builds its partition's table in shared memory and
+ * probes it.  A build partition too large for shared memory (heavily skewed keys) gets its
+ * table in scratch.  Same result as crys_hash_build + crys_probe_aggregate:
+ *   d_sum      one int64: SUM(payload * value) over matching probe rows (wraps mod 2^64)
+ *   d_matches  one int64 counting matching probe rows, or NULL
+ * Keys must be unique (a repeated build key sets CRYS_DEV_DUP_KEY).  nb <= 2^30,
+ * np <= 2^31 - 1.  Scratch (two-call size query): two copies of each side plus 32 bytes per
+ * build row for the oversized-partition tables. */
+int crys_join_partitioned(const int32_t* bkeys, const int32_t* bvals, int64_t nb,
+                          const int32_t* fk, const int32_t* payload, int64_t np, int64_t* d_sum,
+                          int64_t* d_matches, void* d_temp, size_t* temp_bytes, crys_stream s);
 
 /* ------------------------------------------------------------------ query plans
  * Section 5.3: a select-join-aggregate query runs as build kernels for its dimension

@@ -92,6 +92,7 @@ def lib():
         L.crys_strerror.restype = C.c_char_p
         L.crys_device_errors.argtypes = [C.POINTER(C.c_int32), C.c_int, p]
         L.crys_launch_count.restype = i64
+        L.crys_debug_stall.argtypes = [C.c_int, i32, i64]
         L.crys_select.argtypes = [p, i64, i32, i32, p, p, C.c_int, p, sz, p]
         L.crys_select_static.argtypes = [p, i64, i32, i32, p, p, p]
         L.crys_select_strawman.argtypes = [p, i64, i32, i32, p, p, p, sz, p]
@@ -100,6 +101,8 @@ def lib():
         L.crys_hash_build.argtypes = [p, p, i64, C.POINTER(crys_pred), i32, C.POINTER(crys_hash), p]
         L.crys_probe_aggregate.argtypes = [p, p, i64, C.POINTER(crys_hash), p, p, p]
         L.crys_sort.argtypes = [p, p, p, p, i64, p, sz, p]
+        L.crys_sort_msb.argtypes = [p, p, p, p, i64, p, sz, p]
+        L.crys_join_partitioned.argtypes = [p, p, i64, p, p, i64, p, p, p, sz, p]
         L.crys_plan_groups.argtypes = [C.POINTER(crys_plan), C.POINTER(C.c_int64)]
         L.crys_pack_fields.argtypes = [C.POINTER(C.c_void_p), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                        i32, i64, p, p]
@@ -117,9 +120,10 @@ def lib():
         L.crys_tile_variants.argtypes = [C.c_int, C.POINTER(C.c_int32), C.POINTER(C.c_int32), i32]
         L.crys_set_tile.argtypes = [C.c_int, i32]
         L.crys_get_tile.argtypes = [C.c_int]
-        for fn in ("crys_device_errors", "crys_select", "crys_select_static", "crys_select_strawman",
+        for fn in ("crys_device_errors", "crys_debug_stall", "crys_select", "crys_select_static", "crys_select_strawman",
                    "crys_project", "crys_hash_init",
-                   "crys_hash_build", "crys_probe_aggregate", "crys_sort", "crys_plan_groups",
+                   "crys_hash_build", "crys_probe_aggregate", "crys_sort", "crys_sort_msb",
+                   "crys_join_partitioned", "crys_plan_groups",
                    "crys_pack_fields",
                    "crys_run_plan", "crys_run_plans", "crys_run_plans_tagged_bytes",
                    "crys_run_plans_tagged", "crys_tagged_block_bytes", "crys_tagged_prepare",
@@ -165,6 +169,12 @@ def crys_device_errors(clear: bool = True, stream=None) -> int:
 
 def crys_launch_count() -> int:
     return int(lib().crys_launch_count())
+
+
+def crys_debug_stall(op: int, first_tile: int, wait_limit_ns: int) -> None:
+    """Test hook: the next order-preserving select or sort starts its tile ids at
+    first_tile (earlier tiles never publish) and bounds its look-back waits."""
+    _check(lib().crys_debug_stall(op, first_tile, wait_limit_ns), "crys_debug_stall")
 
 
 def crys_select(x, n: int, lo: int, hi: int, out, d_count, order_preserving: int = 0,
@@ -232,6 +242,36 @@ def crys_sort(keys_in, vals_in, keys_out, vals_out, n: int, d_temp=None, temp_by
     tb = C.c_size_t(temp_bytes if temp_bytes is not None else 0)
     _check(lib().crys_sort(_ptr(keys_in), _ptr(vals_in), _ptr(keys_out), _ptr(vals_out), n,
                            _ptr(d_temp), C.byref(tb), _stream(stream)), "crys_sort")
+    return 0
+
+
+def crys_sort_msb(keys_in, vals_in, keys_out, vals_out, n: int, d_temp=None, temp_bytes: int | None = None,
+                  stream=None) -> int:
+    """MSB radix sort (unstable).  Returns the scratch size when d_temp is None and
+    temp_bytes is -1."""
+    if d_temp is None and temp_bytes == -1:
+        size = C.c_size_t(0)
+        _check(lib().crys_sort_msb(None, None, None, None, n, None, C.byref(size), None), "crys_sort_msb")
+        return size.value
+    tb = C.c_size_t(temp_bytes if temp_bytes is not None else 0)
+    _check(lib().crys_sort_msb(_ptr(keys_in), _ptr(vals_in), _ptr(keys_out), _ptr(vals_out), n,
+                               _ptr(d_temp), C.byref(tb), _stream(stream)), "crys_sort_msb")
+    return 0
+
+
+def crys_join_partitioned(bkeys, bvals, nb: int, fk, payload, np_: int, d_sum, d_matches=None, d_temp=None,
+                          temp_bytes: int | None = None, stream=None) -> int:
+    """Radix-partitioned join + SUM(payload * value).  Returns the scratch size when d_temp
+    is None and temp_bytes is -1."""
+    if d_temp is None and temp_bytes == -1:
+        size = C.c_size_t(0)
+        _check(lib().crys_join_partitioned(None, None, nb, None, None, np_, None, None, None, C.byref(size), None),
+               "crys_join_partitioned")
+        return size.value
+    tb = C.c_size_t(temp_bytes if temp_bytes is not None else 0)
+    _check(lib().crys_join_partitioned(_ptr(bkeys), _ptr(bvals), nb, _ptr(fk), _ptr(payload), np_, _ptr(d_sum),
+                                       _ptr(d_matches), _ptr(d_temp), C.byref(tb), _stream(stream)),
+           "crys_join_partitioned")
     return 0
 
 
@@ -410,6 +450,28 @@ def sort(keys: torch.Tensor, vals: torch.Tensor, stream=None):
     temp = scratch(tb, keys.device)
     crys_sort(keys, vals, ko, vo, n, temp, tb, stream)
     return ko, vo
+
+
+def sort_msb(keys: torch.Tensor, vals: torch.Tensor, stream=None):
+    """Unstable MSB radix sort: keys ascending (signed), equal keys' values in any order."""
+    n = keys.numel()
+    ko = torch.empty_like(keys)
+    vo = torch.empty_like(vals)
+    tb = crys_sort_msb(None, None, None, None, n, None, -1)
+    temp = scratch(tb, keys.device)
+    crys_sort_msb(keys, vals, ko, vo, n, temp, tb, stream)
+    return ko, vo
+
+
+def join_partitioned(bkeys: torch.Tensor, bvals: torch.Tensor, fk: torch.Tensor, payload: torch.Tensor,
+                     stream=None):
+    """(SUM(payload * value), matches) of the radix-partitioned join, int64 device tensors."""
+    out = torch.zeros(2, dtype=torch.int64, device=fk.device)
+    tb = crys_join_partitioned(None, None, bkeys.numel(), None, None, fk.numel(), None, None, None, -1)
+    temp = scratch(tb, fk.device)
+    crys_join_partitioned(bkeys, bvals, bkeys.numel(), fk, payload, fk.numel(), out[0:1], out[1:2], temp, tb,
+                          stream)
+    return out[0:1], out[1:2]
 
 
 def make_table(cols: list) -> crys_table:

@@ -20,6 +20,11 @@ int32_t* g_error_ptr[kMaxDevices] = {};
 int g_sms[kMaxDevices] = {};
 std::atomic<int64_t> g_launches{0};
 std::atomic<int> g_variant[CRYS_NUM_OPS] = {};
+// pending crys_debug_stall request (op, first tile, wait bound), taken by the next call
+std::mutex g_stall_mutex;
+int g_stall_op = -1;
+uint32_t g_stall_first = 0;
+uint64_t g_stall_ns = 0;
 
 int current_device() {
   int dev = 0;
@@ -67,6 +72,17 @@ bool set_dynamic_smem(const void* kernel, size_t bytes) {
   return true;
 }
 
+bool take_stall(int op, uint32_t* first_tile, uint64_t* wait_ns) {
+  std::lock_guard<std::mutex> lock(g_stall_mutex);
+  *first_tile = 0;
+  *wait_ns = kWaitBoundNs;
+  if (g_stall_op != op) return false;
+  *first_tile = g_stall_first;
+  *wait_ns = g_stall_ns;
+  g_stall_op = -1;
+  return true;
+}
+
 int tile_variant(int op) {
   if (op < 0 || op >= CRYS_NUM_OPS) return 0;
   return g_variant[op].load(std::memory_order_relaxed);
@@ -103,6 +119,17 @@ int crys_device_errors(int32_t* flags, int clear, crys_stream s) {
 }
 
 int64_t crys_launch_count(void) { return crys::g_launches.load(); }
+
+int crys_debug_stall(int op, int32_t first_tile, int64_t wait_limit_ns) {
+  if ((op != CRYS_OP_SELECT && op != CRYS_OP_SORT) || first_tile < 0 || wait_limit_ns < 1000 ||
+      wait_limit_ns > static_cast<int64_t>(crys::kWaitBoundNs))
+    return CRYS_EINVAL;
+  std::lock_guard<std::mutex> lock(crys::g_stall_mutex);
+  crys::g_stall_op = op;
+  crys::g_stall_first = static_cast<uint32_t>(first_tile);
+  crys::g_stall_ns = static_cast<uint64_t>(wait_limit_ns);
+  return CRYS_OK;
+}
 
 int crys_tile_variants(int op, int32_t* threads, int32_t* items, int32_t max) {
   if (op < 0 || op >= CRYS_NUM_OPS) return CRYS_EINVAL;

@@ -207,8 +207,10 @@ __global__ void __launch_bounds__(THREADS) probe_kernel(ProbeArgs a) {
       issue(s);
     }
   }
-  if (aborted) return;
-  // BlockAggregate: one atomic per block for the sum and one for the match count.
+  // BlockAggregate: one atomic per block for the sum and one for the match count.  A block
+  // whose stage wait ran out (CRYS_DEV_TIMEOUT is set) still adds the rows it did finish,
+  // so the partial result and the error flag arrive together.
+  (void)aborted;
   const uint64_t bsum = block_sum_u64<THREADS>(sum, red);
   const uint64_t bmatch = block_sum_u64<THREADS>(matches, red);
   if (tid == 0) {

@@ -20,6 +20,11 @@ int sm_count();
 // Current tile variant of an operator (index into its variant table).
 int tile_variant(int op);
 
+// The stall requested by crys_debug_stall for the next call of `op`, consumed by this
+// call: tile ids start at *first_tile and look-back waits give up after *wait_ns.
+// Without a request: 0 and the default bound.  Returns whether a request was taken.
+bool take_stall(int op, uint32_t* first_tile, uint64_t* wait_ns);
+
 inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
 inline int check_launch() { return cudaGetLastError() == cudaSuccess ? CRYS_OK : CRYS_ECUDA; }

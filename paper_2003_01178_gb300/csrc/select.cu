@@ -40,15 +40,19 @@ struct SelectArgs {
   int32_t* out;
   unsigned long long* count;  // cursor (mode 0) / final count (mode 1)
   uint64_t* tile_state;       // mode 1: one status word per tile
-  unsigned int* tile_counter; // mode 1: next tile id
+  unsigned int* tile_counter; // mode 1: next tile id (scratch header, word 0)
+  unsigned int* abort_word;   // mode 1: set by the first block of this call that gives up
+  uint32_t tile_base;         // mode 1: first tile id handed out (0 unless a test stalls)
+  uint64_t wait_ns;           // mode 1: bound of a look-back wait
   int32_t* err;
   int32_t stages;
 };
 
 // Decoupled look-back over tiles 0..t-1 (thread 0 only).  Returns the number of
 // selected rows in all earlier tiles, or -1 if a predecessor never published within
-// the wait bound (or another block already reported a failure).
-__device__ int64_t lookback_exclusive(uint64_t* state, int64_t t, uint64_t total, int32_t* err) {
+// the wait bound, or another block of the same call already gave up (its abort word,
+// in this call's scratch: a failure of an earlier call does not reach this one).
+__device__ int64_t lookback_exclusive(uint64_t* state, int64_t t, uint64_t total, const SelectArgs& a) {
   if (t == 0) {
     st_relaxed_u64(&state[0], kFlagInclusive | total);
     return 0;
@@ -65,11 +69,12 @@ __device__ int64_t lookback_exclusive(uint64_t* state, int64_t t, uint64_t total
       if (!timing) {
         t0 = global_timer_ns();
         timing = true;
-      } else if (global_timer_ns() - t0 > kWaitBoundNs) {
-        set_error(err, CRYS_DEV_TIMEOUT);
+      } else if (global_timer_ns() - t0 > a.wait_ns) {
+        set_error(a.err, CRYS_DEV_TIMEOUT);
+        st_relaxed_u32(a.abort_word, 1u);
         return -1;
       }
-      if (read_error(err) & CRYS_DEV_TIMEOUT) return -1;
+      if (ld_relaxed_u32(a.abort_word)) return -1;
       continue;
     }
     timing = false;
@@ -106,7 +111,7 @@ __global__ void __launch_bounds__(THREADS) select_kernel(SelectArgs a) {
   int64_t issued = 0;  // thread 0 only
 
   auto issue = [&](int s) {
-    int64_t t = ORDERED ? static_cast<int64_t>(atomicAdd(a.tile_counter, 1u))
+    int64_t t = ORDERED ? static_cast<int64_t>(a.tile_base) + static_cast<int64_t>(atomicAdd(a.tile_counter, 1u))
                         : static_cast<int64_t>(blockIdx.x) + issued * gridDim.x;
     ++issued;
     if (t >= ntiles) {
@@ -213,7 +218,7 @@ __global__ void __launch_bounds__(THREADS) select_kernel(SelectArgs a) {
       if (lane == 0) {
         long long base;
         if (ORDERED) {
-          base = lookback_exclusive(a.tile_state, t, static_cast<uint64_t>(total), a.err);
+          base = lookback_exclusive(a.tile_state, t, static_cast<uint64_t>(total), a);
           if (base >= 0 && t == ntiles - 1) *a.count = static_cast<unsigned long long>(base + total);
         } else {
           base = total ? static_cast<long long>(atomicAdd(a.count, static_cast<unsigned long long>(total))) : 0;
@@ -305,12 +310,17 @@ extern "C" int crys_select(const int32_t* x, int64_t n, int32_t lo, int32_t hi, 
   a.out = out;
   a.count = reinterpret_cast<unsigned long long*>(d_count);
   a.tile_counter = nullptr;
+  a.abort_word = nullptr;
   a.tile_state = nullptr;
+  a.tile_base = 0;
+  a.wait_ns = kWaitBoundNs;
   a.err = device_error_word();
   if (!a.err) return CRYS_ECUDA;
   if (order_preserving) {
     a.tile_counter = static_cast<unsigned int*>(d_temp);
+    a.abort_word = static_cast<unsigned int*>(d_temp) + 1;
     a.tile_state = reinterpret_cast<uint64_t*>(static_cast<char*>(d_temp) + 256);
+    take_stall(CRYS_OP_SELECT, &a.tile_base, &a.wait_ns);
     if (cudaMemsetAsync(d_temp, 0, need, s) != cudaSuccess) return CRYS_ECUDA;
   }
   const bool ord = order_preserving != 0;

@@ -100,6 +100,9 @@ struct PassArgs {
   const unsigned int* digit_base;  // 256 bucket starts of this pass
   uint32_t* status;                // per tile x digit look-back words
   unsigned int* tile_counter;
+  unsigned int* abort_word;        // set by the first block of this sort that gives up
+  uint32_t tile_base;              // first tile id handed out (0 unless a test stalls)
+  uint64_t wait_ns;                // bound of a look-back wait
   int32_t* err;
 };
 
@@ -121,13 +124,15 @@ __global__ void __launch_bounds__(THREADS) sort_pass_kernel(PassArgs a) {
 
   const int tid = threadIdx.x, lane = tid % kWarp, warp = tid / kWarp;
   if (tid == 0) {
-    tile_sh = atomicAdd(a.tile_counter, 1u);
+    // a sort whose earlier pass gave up does no further work (tile id past the end)
+    tile_sh = ld_relaxed_u32(a.abort_word) ? 0xFFFFFFFFu : a.tile_base + atomicAdd(a.tile_counter, 1u);
     mbar_init(&loaded, 1);
     fence_barrier_init();
   }
   for (int i = tid; i < WARPS * kRadix; i += THREADS) (&whist[0][0])[i] = 0;
   __syncthreads();
   const int64_t tile = tile_sh;
+  if (tile * TILE >= a.n) return;  // nothing issued on the barrier yet
   const int64_t tile_row = tile * TILE;
   const int valid = static_cast<int>((a.n - tile_row) < TILE ? (a.n - tile_row) : TILE);
   const int bulk = valid & ~3;
@@ -227,12 +232,13 @@ __global__ void __launch_bounds__(THREADS) sort_pass_kernel(PassArgs a) {
           if (!timing) {
             t0 = global_timer_ns();
             timing = true;
-          } else if (global_timer_ns() - t0 > kWaitBoundNs) {
+          } else if (global_timer_ns() - t0 > a.wait_ns) {
             set_error(a.err, CRYS_DEV_TIMEOUT);
+            st_relaxed_u32(a.abort_word, 1u);
             failed = true;
             break;
           }
-          if (read_error(a.err) & CRYS_DEV_TIMEOUT) {
+          if (ld_relaxed_u32(a.abort_word)) {  // another block of this sort gave up
             failed = true;
             break;
           }
@@ -343,9 +349,15 @@ int run_passes(const int32_t* keys_in, const int32_t* vals_in, int32_t* keys_out
   PassArgs a;
   a.n = n;
   a.status = reinterpret_cast<uint32_t*>(temp + L.status);
+  a.abort_word = reinterpret_cast<unsigned int*>(temp + L.counters) + kPasses;
   a.err = device_error_word();
   if (!a.err) return CRYS_ECUDA;
+  uint32_t stall_base = 0;
+  uint64_t stall_ns = kWaitBoundNs;
+  take_stall(CRYS_OP_SORT, &stall_base, &stall_ns);  // a test's stall applies to the first pass
   for (int p = 0; p < kPasses; ++p) {
+    a.tile_base = p == 0 ? stall_base : 0u;
+    a.wait_ns = p == 0 ? stall_ns : kWaitBoundNs;
     a.keys_in = src_k[p];
     a.vals_in = src_v[p];
     a.keys_out = dst_k[p];

@@ -167,3 +167,12 @@ def test_replayable_launch_host_checks(crys):
     assert L.crys_tagged_prepare(C.byref(t), arr, 1, 2, 100, 0, z, 0, C.c_void_p(4096), 64, hb) == crys.EINVAL
     assert L.crys_tagged_launch(None, None) == crys.EINVAL
     del args
+
+
+def test_debug_stall_arguments(crys):
+    """The wait-bound test hook validates its arguments on the host."""
+    L = crys.lib()
+    assert L.crys_debug_stall(crys.OP_PROJECT, 1, 1_000_000) == crys.EINVAL
+    assert L.crys_debug_stall(crys.OP_SELECT, -1, 1_000_000) == crys.EINVAL
+    assert L.crys_debug_stall(crys.OP_SELECT, 1, 10) == crys.EINVAL
+    assert L.crys_debug_stall(crys.OP_SORT, 1, 3_000_000_000) == crys.EINVAL

@@ -66,3 +66,51 @@ def test_host_rejections_enqueue_nothing(crys):
     with pytest.raises(crys.CrystalError):
         crys.crys_sort(x, x, x, x, 16, torch.empty(16, dtype=torch.uint8, device="cuda"), 16)
     assert crys.crys_launch_count() == before
+
+
+def _flags(crys, clear=False):
+    return crys.crys_device_errors(clear=clear)
+
+
+def test_select_lookback_timeout_is_reported_and_stays_in_its_call(crys, orc):
+    """A predecessor tile that never publishes (tile ids start at 5): the order-preserving
+    selection's look-back gives up after its 2 ms bound, the call returns promptly with
+    CRYS_DEV_TIMEOUT set, and a later call - with the error word NOT cleared - is exact."""
+    import time
+    import datagen
+    crys.crys_device_errors(clear=True)
+    x = torch.from_numpy(datagen.uniform_i32(9, datagen.STREAMS["sel.x"], 1 << 22, 0, (1 << 31) - 1)).cuda()
+    hi = datagen.select_threshold(0.5)
+    crys.crys_debug_stall(crys.OP_SELECT, 5, 2_000_000)
+    t0 = time.perf_counter()
+    got = crys.select(x, -(1 << 31), hi, order_preserving=True)   # synchronises on the count
+    elapsed = time.perf_counter() - t0
+    assert elapsed < 1.5, elapsed
+    assert _flags(crys) & crys.DEV_TIMEOUT
+    assert got.numel() < x.numel()                  # the call's output is incomplete
+    # the next call carries no abort from the one that gave up
+    got = crys.select(x, -(1 << 31), hi, order_preserving=True).cpu().numpy()
+    assert np.array_equal(got, orc.select(x.cpu().numpy(), -(1 << 31), hi))
+    assert _flags(crys, clear=True) == crys.DEV_TIMEOUT   # only the stalled call's bit
+    assert _flags(crys) == 0
+
+
+def test_sort_lookback_timeout_is_reported_and_stays_in_its_call(crys, orc):
+    import time
+    import datagen
+    crys.crys_device_errors(clear=True)
+    n = 300_001
+    keys = torch.from_numpy(datagen.bits_i32(9, datagen.STREAMS["sort.key"], n)).cuda()
+    vals = torch.arange(n, dtype=torch.int32, device="cuda")
+    crys.crys_debug_stall(crys.OP_SORT, 3, 2_000_000)
+    t0 = time.perf_counter()
+    crys.sort(keys, vals)
+    torch.cuda.synchronize()
+    assert time.perf_counter() - t0 < 1.5
+    assert _flags(crys) & crys.DEV_TIMEOUT
+    ko, vo = crys.sort(keys, vals)
+    rk, rv = orc.sort(keys.cpu().numpy(), vals.cpu().numpy())
+    assert np.array_equal(ko.cpu().numpy(), rk) and np.array_equal(vo.cpu().numpy(), rv)
+    assert _flags(crys, clear=True) == crys.DEV_TIMEOUT
+    assert _flags(crys) == 0
+

@@ -75,6 +75,7 @@ def test_project_full_size_sampled(crys, orc):
 
 @pytest.mark.parametrize("lg", [10, 27])
 def test_join_full_size(crys, orc, threads, lg):
+    """The direct probe and the radix-partitioned join, both against the oracle."""
     import datagen.device as dgd
     nb, n = 1 << lg, 1 << 28
     bk = dgd.perm_i32(SEED, datagen.STREAMS["join.bkey"], nb)
@@ -86,6 +87,9 @@ def test_join_full_size(crys, orc, threads, lg):
     ref = orc.join_sum(bk.cpu().numpy(), bv.cpu().numpy(), fk.cpu().numpy(), pay.cpu().numpy(), threads=threads)
     assert (int(s.item()), int(m.item())) == ref
     assert int(m.item()) == n                    # every foreign key names a build key
+    del ht
+    s, m = crys.join_partitioned(bk, bv, fk, pay)
+    assert (int(s.item()), int(m.item())) == ref
 
 
 def test_sort_full_size_properties(crys):
@@ -104,6 +108,23 @@ def test_sort_full_size_properties(crys):
     seen[v] = 1
     assert seen.all()                                         # row ids a permutation
     assert np.array_equal(kin[v], k.astype(np.int32))         # each pair is an input pair
+
+
+def test_msb_sort_full_size_properties(crys):
+    """The unstable MSB sort at 2^28 keys: ordered keys, row ids a permutation, and each
+    output pair an input pair (what fixes an unstable sort's result)."""
+    import datagen.device as dgd
+    n = 1 << 28
+    keys = dgd.bits_i32(SEED, datagen.STREAMS["sort.key"], n)
+    vals = torch.arange(n, dtype=torch.int32, device="cuda")
+    ko, vo = crys.sort_msb(keys, vals)
+    k = ko.cpu().numpy()
+    v = vo.cpu().numpy().astype(np.int64)
+    assert np.all(np.diff(k.astype(np.int64)) >= 0)
+    seen = np.zeros(n, np.uint8)
+    seen[v] = 1
+    assert seen.all()
+    assert np.array_equal(keys.cpu().numpy()[v], k)
 
 
 def test_q1_full_size(crys, orc, threads):
