@@ -23,7 +23,7 @@ namespace {
 
 constexpr int kBuckets = 256;
 constexpr int kPartThreads = 256;
-constexpr int kPartItems = 16;
+constexpr int kPartItems = 8;
 constexpr int kPartTile = kPartThreads * kPartItems;  // rows per tile of a partition pass
 
 // Digit of a key: ((key * mult) >> shift) & mask, then XOR flip.  Sort digits use
@@ -37,11 +37,13 @@ struct DigitFn {
 };
 
 // Segments of a pass: segment s covers rows [begin[s], begin[s] + size[s]) and owns the
-// tiles [tile_start[s], tile_start[s + 1]) of the pass (tile_start has count + 1 entries).
+// tiles [tile_start[s], tile_start[s + 1]) of the pass (tile_start has count + 1 entries);
+// tile_seg[b] is the segment of tile b (unused when there is one segment).
 struct Segs {
   const int64_t* begin;
   const int64_t* size;
   const uint32_t* tile_start;
+  const uint32_t* tile_seg;
   int32_t count;
 };
 
@@ -55,12 +57,7 @@ struct TileAt {
 __device__ __forceinline__ TileAt find_tile(const Segs& S, uint32_t b, int tile_rows) {
   TileAt r{-1, 0, 0};
   if (b >= S.tile_start[S.count]) return r;
-  int lo = 0, hi = S.count;  // tile_start[lo] <= b < tile_start[hi]
-  while (hi - lo > 1) {
-    const int mid = (lo + hi) >> 1;
-    if (S.tile_start[mid] <= b) lo = mid;
-    else hi = mid;
-  }
+  const int lo = S.count == 1 ? 0 : static_cast<int>(S.tile_seg[b]);
   const int64_t t = static_cast<int64_t>(b - S.tile_start[lo]);
   const int64_t rem = S.size[lo] - t * tile_rows;
   r.seg = lo;
@@ -102,10 +99,11 @@ __global__ void seg_init_kernel(int64_t n, int tile_rows, int64_t* begin, int64_
 }
 
 // The buckets of a pass as the segments of the next one: begin/size from the bucket
-// starts and counts, and their tile prefix (one block of 1024 threads, any count).
+// starts and counts, their tile prefix and the segment of every tile (one block of 1024
+// threads, any count).
 __global__ void __launch_bounds__(1024) seg_from_buckets_kernel(const int64_t* bucket_begin, const uint32_t* bucket_count,
                                                                 int n, int tile_rows, int64_t* begin, int64_t* size,
-                                                                uint32_t* tile_start) {
+                                                                uint32_t* tile_start, uint32_t* tile_seg) {
   __shared__ uint32_t tmp[kWarp + 1];
   __shared__ uint32_t carry;
   if (threadIdx.x == 0) carry = 0;
@@ -126,6 +124,9 @@ __global__ void __launch_bounds__(1024) seg_from_buckets_kernel(const int64_t* b
     __syncthreads();
   }
   if (threadIdx.x == 0) tile_start[n] = carry;
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += 1024)
+    for (uint32_t t = tile_start[i]; t < tile_start[i + 1]; ++t) tile_seg[t] = static_cast<uint32_t>(i);
 }
 
 // ---------------------------------------------------------------- one partition pass
@@ -295,9 +296,10 @@ __global__ void __launch_bounds__(kPartThreads) part_scatter_kernel(const __grid
 // (stable).  The sorted rows are then gathered from the bucket in global memory (it was
 // just read, so L2 serves the gather) and stored with consecutive addresses.
 
-constexpr int kLocalThreads = 512;
-constexpr int kLocalIpt = 16;
-constexpr int kLocalCap = kLocalThreads * kLocalIpt;  // 8192 rows: 13-bit row index
+constexpr int kLocalThreads = 256;
+constexpr int kLocalIpt = 20;
+constexpr int kLocalCap = kLocalThreads * kLocalIpt;  // 5120 rows: a 13-bit row index
+static_assert(kLocalCap <= 8192 && kLocalIpt <= 255, "13-bit rows, 8-bit per-thread digit counters");
 constexpr int kLocalPad = kLocalIpt + 1;              // words per thread slice incl. one pad word
 
 // Position p of the sorted order in the padded layout (one pad word per 16 words, so that
@@ -329,6 +331,7 @@ __device__ __forceinline__ void local_pass(const uint32_t* src, uint32_t* dst, i
   __syncthreads();
   // exclusive scan of the 16 x kLocalThreads counters in (digit, thread) order: each
   // thread takes 16 consecutive counters, then one block scan of the threads' sums
+  static_assert(16 * kLocalThreads % kLocalThreads == 0, "16 counters per thread");
   uint32_t loc[16];
   uint32_t sum = 0;
 #pragma unroll
@@ -664,29 +667,31 @@ struct Level {
   int64_t* seg_begin;
   int64_t* seg_size;
   uint32_t* tile_start;
+  uint32_t* tile_seg;         // [tiles]
   uint32_t* hist;             // [segments][256]
   unsigned long long* cursor;  // [segments][256]
   int64_t* bucket_begin;      // [segments * 256]
 };
 
-Level carve_level(Carve& c, int segments) {
+int64_t tiles_bound(int64_t n, int segments, int tile_rows) { return (n + tile_rows - 1) / tile_rows + segments; }
+
+Level carve_level(Carve& c, int segments, int64_t rows) {
   Level L;
   L.seg_begin = c.take<int64_t>(segments);
   L.seg_size = c.take<int64_t>(segments);
   L.tile_start = c.take<uint32_t>(segments + 1);
+  L.tile_seg = c.take<uint32_t>(static_cast<size_t>(tiles_bound(rows, segments, kPartTile)));
   L.hist = c.take<uint32_t>(static_cast<size_t>(segments) * kBuckets);
   L.cursor = c.take<unsigned long long>(static_cast<size_t>(segments) * kBuckets);
   L.bucket_begin = c.take<int64_t>(static_cast<size_t>(segments) * kBuckets);
   return L;
 }
 
-int64_t tiles_bound(int64_t n, int segments, int tile_rows) { return (n + tile_rows - 1) / tile_rows + segments; }
-
 // One partition pass over the segments of L (already set up): histogram, scan, scatter.
 int run_pass(const Level& L, int segments, int64_t n, const int32_t* kin, const int32_t* vin, int32_t* kout,
              int32_t* vout, DigitFn f, int32_t* err, cudaStream_t s) {
   if (cudaMemsetAsync(L.hist, 0, static_cast<size_t>(segments) * kBuckets * 4, s) != cudaSuccess) return CRYS_ECUDA;
-  Segs S{L.seg_begin, L.seg_size, L.tile_start, segments};
+  Segs S{L.seg_begin, L.seg_size, L.tile_start, L.tile_seg, segments};
   const int64_t grid = tiles_bound(n, segments, kPartTile);
   part_hist_kernel<<<static_cast<unsigned>(grid), kPartThreads, 0, s>>>(kin, S, f, L.hist);
   note_launch();
@@ -728,8 +733,8 @@ extern "C" int crys_sort_msb(const int32_t* keys_in, const int32_t* vals_in, int
     Carve c(base);
     *tk = c.take<int32_t>(static_cast<size_t>(n));
     *tv = c.take<int32_t>(static_cast<size_t>(n));
-    *A = carve_level(c, 1);
-    *B = carve_level(c, kBuckets);
+    *A = carve_level(c, 1, n);
+    *B = carve_level(c, kBuckets, n);
     return c.off;
   };
   int32_t *tk, *tv;
@@ -759,7 +764,7 @@ extern "C" int crys_sort_msb(const int32_t* keys_in, const int32_t* vals_in, int
   if (rc != CRYS_OK) return rc;
   // level B: each of the 256 buckets by the next digit, output -> scratch buffers
   seg_from_buckets_kernel<<<1, 1024, 0, s>>>(A.bucket_begin, A.hist, kBuckets, kPartTile, B.seg_begin, B.seg_size,
-                                             B.tile_start);
+                                             B.tile_start, B.tile_seg);
   note_launch();
   rc = run_pass(B, kBuckets, n, keys_out, vals_out, tk, tv, DigitFn{1u, 16u, 0xFFu, 0u}, err, s);
   if (rc != CRYS_OK) return rc;
@@ -792,6 +797,7 @@ extern "C" int crys_join_partitioned(const int32_t* bkeys, const int32_t* bvals,
     int64_t* p_begin;
     int64_t* p_size;
     uint32_t* p_tiles;
+    uint32_t* p_tile_seg;
     uint64_t* arena;
   };
   auto layout = [&](void* base, Side* R, Side* P, Parts* J) {
@@ -802,14 +808,15 @@ extern "C" int crys_join_partitioned(const int32_t* bkeys, const int32_t* bvals,
       sd->v1 = c.take<int32_t>(rows);
       sd->k2 = c.take<int32_t>(rows);
       sd->v2 = c.take<int32_t>(rows);
-      sd->A = carve_level(c, 1);
-      sd->B = carve_level(c, parts1);
+      sd->A = carve_level(c, 1, static_cast<int64_t>(rows));
+      sd->B = carve_level(c, parts1, static_cast<int64_t>(rows));
     }
     J->b_begin = c.take<int64_t>(1);
     J->b_count = c.take<uint32_t>(1);
     J->p_begin = c.take<int64_t>(static_cast<size_t>(parts));
     J->p_size = c.take<int64_t>(static_cast<size_t>(parts));
     J->p_tiles = c.take<uint32_t>(static_cast<size_t>(parts) + 1);
+    J->p_tile_seg = c.take<uint32_t>(static_cast<size_t>(tiles_bound(np, parts, kJoinTile)));
     J->arena = c.take<uint64_t>(static_cast<size_t>(4) * static_cast<size_t>(nb > 0 ? nb : 1));
     return c.off;
   };
@@ -855,7 +862,7 @@ extern "C" int crys_join_partitioned(const int32_t* bkeys, const int32_t* bvals,
     fin_count[w] = sd.A.hist;
     if (b2 == 0) continue;
     seg_from_buckets_kernel<<<1, 1024, 0, s>>>(sd.A.bucket_begin, sd.A.hist, parts1, kPartTile, sd.B.seg_begin,
-                                               sd.B.seg_size, sd.B.tile_start);
+                                               sd.B.seg_size, sd.B.tile_start, sd.B.tile_seg);
     note_launch();
     rc = run_pass(sd.B, parts1, rows[w], sd.k1, sd.v1, sd.k2, sd.v2, f2, err, s);
     if (rc != CRYS_OK) return rc;
@@ -873,7 +880,7 @@ extern "C" int crys_join_partitioned(const int32_t* bkeys, const int32_t* bvals,
     b_count = J.b_count;
   } else {
     seg_from_buckets_kernel<<<1, 1024, 0, s>>>(fin_begin[1], fin_count[1], parts, kJoinTile, J.p_begin, J.p_size,
-                                               J.p_tiles);
+                                               J.p_tiles, J.p_tile_seg);
     note_launch();
   }
   JoinArgs a;
@@ -883,7 +890,7 @@ extern "C" int crys_join_partitioned(const int32_t* bkeys, const int32_t* bvals,
   a.b_count = b_count;
   a.pkey = fin_k[1];
   a.ppay = fin_v[1];
-  a.probe = Segs{J.p_begin, J.p_size, J.p_tiles, parts};
+  a.probe = Segs{J.p_begin, J.p_size, J.p_tiles, J.p_tile_seg, parts};
   a.arena = J.arena;
   a.sum = reinterpret_cast<unsigned long long*>(d_sum);
   a.matches = reinterpret_cast<unsigned long long*>(d_matches);
