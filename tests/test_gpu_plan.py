@@ -29,8 +29,11 @@ def _dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
-def _q1_gpu(crys, fact, dim, year=3):
-    ht = crys.HashTable.build(dim["key"], dim["yr"], filters=[(dim["yr"], year, year)])
+def _q1_gpu(crys, fact, dim, year=3, kind=0):
+    # kind 0: multiplicative hashing with linear probing; 2: a direct table (the dense date
+    # keys' perfect hashing)
+    cap = dim["key"].numel() if kind == crys.HASH_DIRECT else None
+    ht = crys.HashTable.build(dim["key"], dim["yr"], filters=[(dim["yr"], year, year)], capacity=cap, kind=kind)
     sums, counts = crys.run_plan([fact["fk"], fact["a"], fact["b"], fact["c"]],
                                  [(1, I32_MIN, 24), (2, 1, 3)], [(0, ht, 0)], ("mul", 3, 2))
     return int(sums[0].item()), int(counts[0].item())
@@ -38,12 +41,13 @@ def _q1_gpu(crys, fact, dim, year=3):
 
 @pytest.mark.parametrize("n", [0, 1, 5, 1023, 4096, 4099, 100_003, 1 << 22, (1 << 24) + 3])
 @pytest.mark.parametrize("variant", range(4))
-def test_q1_parity(crys, orc, n, variant):
+@pytest.mark.parametrize("kind", [0, 2])
+def test_q1_parity(crys, orc, n, variant, kind):
     crys.crys_set_tile(crys.OP_PLAN, variant)
     host = datagen.q1_tables(40 + n % 7, n)
     fact = {k: _dev(v) for k, v in host["fact"].items()}
     dim = {k: _dev(v) for k, v in host["dim"].items()}
-    s, c = _q1_gpu(crys, fact, dim)
+    s, c = _q1_gpu(crys, fact, dim, kind=kind)
     assert s == orc.q1_run(host["fact"], host["dim"])
     crys.crys_set_tile(crys.OP_PLAN, 0)
 
