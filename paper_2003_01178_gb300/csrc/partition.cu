@@ -131,43 +131,51 @@ __global__ void __launch_bounds__(1024) seg_from_buckets_kernel(const int64_t* b
 
 // ---------------------------------------------------------------- one partition pass
 
+// Digit counts of every segment.  A persistent block takes a contiguous range of the
+// pass's tiles (so it stays in one segment for many tiles), counts in shared memory and
+// adds its counts to the segment's when the segment changes and at the end.
 __global__ void __launch_bounds__(kPartThreads) part_hist_kernel(const int32_t* __restrict__ keys, Segs S, DigitFn f,
                                                                  uint32_t* hist) {
   constexpr int kCopies = 4;
   __shared__ uint32_t h[kCopies][kBuckets];
-  __shared__ int seg_sh;
-  __shared__ long long row0_sh;
-  __shared__ int valid_sh;
   const int tid = threadIdx.x;
   for (int i = tid; i < kCopies * kBuckets; i += kPartThreads) (&h[0][0])[i] = 0;
-  if (tid == 0) {
-    const TileAt at = find_tile(S, blockIdx.x, kPartTile);
-    seg_sh = at.seg;
-    row0_sh = at.row0;
-    valid_sh = at.valid;
-  }
-  __syncthreads();
-  const int seg = seg_sh;
-  if (seg < 0) return;
-  const int64_t row0 = row0_sh;
-  const int valid = valid_sh;
+  const uint32_t total = S.tile_start[S.count];
+  const uint32_t t0 = static_cast<uint32_t>((static_cast<uint64_t>(total) * blockIdx.x) / gridDim.x);
+  const uint32_t t1 = static_cast<uint32_t>((static_cast<uint64_t>(total) * (blockIdx.x + 1)) / gridDim.x);
   uint32_t* mine = h[(tid / kWarp) % kCopies];
-  int32_t k[kPartItems];
+  int cur = -1;
+  auto flush = [&](int seg) {
+    __syncthreads();
+    for (int d = tid; d < kBuckets; d += kPartThreads) {
+      uint32_t c = 0;
 #pragma unroll
-  for (int i = 0; i < kPartItems; ++i) {
-    const int idx = i * kPartThreads + tid;
-    k[i] = idx < valid ? keys[row0 + idx] : 0;
-  }
-#pragma unroll
-  for (int i = 0; i < kPartItems; ++i)
-    if (i * kPartThreads + tid < valid) atomicAdd(&mine[f(k[i])], 1u);
+      for (int r = 0; r < kCopies; ++r) {
+        c += h[r][d];
+        h[r][d] = 0;
+      }
+      if (c) atomicAdd(&hist[static_cast<int64_t>(seg) * kBuckets + d], c);
+    }
+    __syncthreads();
+  };
   __syncthreads();
-  for (int d = tid; d < kBuckets; d += kPartThreads) {
-    uint32_t c = 0;
+  for (uint32_t b = t0; b < t1; ++b) {
+    const TileAt at = find_tile(S, b, kPartTile);  // every thread: the same few cached words
+    if (at.seg != cur) {
+      if (cur >= 0) flush(cur);
+      cur = at.seg;
+    }
+    int32_t k[kPartItems];
 #pragma unroll
-    for (int r = 0; r < kCopies; ++r) c += h[r][d];
-    if (c) atomicAdd(&hist[static_cast<int64_t>(seg) * kBuckets + d], c);
+    for (int i = 0; i < kPartItems; ++i) {
+      const int idx = i * kPartThreads + tid;
+      k[i] = idx < at.valid ? keys[at.row0 + idx] : 0;
+    }
+#pragma unroll
+    for (int i = 0; i < kPartItems; ++i)
+      if (i * kPartThreads + tid < at.valid) atomicAdd(&mine[f(k[i])], 1u);
   }
+  if (cur >= 0) flush(cur);
 }
 
 // Bucket starts of every segment: begin of the segment plus the exclusive prefix of its
@@ -493,10 +501,13 @@ constexpr size_t kLocalSmem = (2 * kLocalThreads * kLocalPad + 16 * kLocalThread
 //
 // After both sides are partitioned by the same hash bits, build partition p's table in
 // shared memory (linear probing, capacity a power of two of at least twice its rows, at
-// most kJoinSlots) and probe a tile of probe partition p against it.  A build partition
-// too large for shared memory gets a table in global scratch at 4 x its first row (its
-// capacity is at most 4 x its rows, so the regions of different partitions do not
-// overlap).  Each block adds its sum and matches with one atomic each.
+// most kJoinSlots) and probe the tiles of probe partition p against it.  Persistent
+// blocks take contiguous ranges of probe tiles, so a block works through whole
+// partitions in order, builds each table once, and has the copy engine bring the next
+// tile's rows into L2 while it probes.  A build partition too large for shared memory
+// gets a table in global scratch at 4 x its first row (its capacity is at most 4 x its
+// rows, so the regions of different partitions do not overlap), built beforehand.  Each
+// block adds its sum and matches with one atomic each.
 
 constexpr int kJoinThreads = 512;
 constexpr int kJoinItems = 16;
@@ -583,58 +594,71 @@ __global__ void __launch_bounds__(kJoinThreads) join_build_large_kernel(const __
   join_insert(a, bb, bn, table, cap, kJoinThreads);
 }
 
-__global__ void __launch_bounds__(kJoinThreads) join_partition_kernel(const __grid_constant__ JoinArgs a) {
+// Bulk L2 prefetch of rows [row, row + rows) of a column (whole 16-byte groups inside the
+// range; a partial group at either end is left to the demand loads).
+__device__ __forceinline__ void prefetch_rows(const int32_t* col, int64_t row, int64_t rows) {
+  const int64_t first = (row + 3) & ~int64_t{3}, last = (row + rows) & ~int64_t{3};
+  if (last > first) bulk_prefetch_l2(col + first, static_cast<uint32_t>((last - first) * 4));
+}
+
+__global__ void __launch_bounds__(kJoinThreads, 2) join_partition_kernel(const __grid_constant__ JoinArgs a) {
   extern __shared__ __align__(16) uint64_t stab[];  // kJoinSlots slots
   __shared__ uint64_t red[kJoinThreads / kWarp];
-  __shared__ int seg_sh;
-  __shared__ long long row0_sh;
-  __shared__ int valid_sh;
   const int tid = threadIdx.x;
-  if (tid == 0) {
-    const TileAt at = find_tile(a.probe, blockIdx.x, kJoinTile);
-    seg_sh = at.seg;
-    row0_sh = at.row0;
-    valid_sh = at.valid;
-  }
-  __syncthreads();
-  const int p = seg_sh;
-  if (p < 0) return;
-  const int64_t row0 = row0_sh;
-  const int valid = valid_sh;
-  const int64_t bb = a.b_begin[p];
-  const uint32_t bn = a.b_count[p];
-  const uint32_t cap = join_capacity(bn);
-  const bool in_smem = cap <= static_cast<uint32_t>(kJoinSlots);
-  const uint64_t* table = in_smem ? stab : a.arena + 4 * bb;  // the arena's table is built already
-  const uint32_t mask = cap - 1;
-  // the probe tile's rows are loaded while the table is built
-  int32_t k[kJoinItems], pay[kJoinItems];
-#pragma unroll
-  for (int i = 0; i < kJoinItems; ++i) {
-    const int idx = i * kJoinThreads + tid;
-    k[i] = idx < valid ? a.pkey[row0 + idx] : 0;
-    pay[i] = idx < valid ? a.ppay[row0 + idx] : 0;
-  }
-  if (in_smem) {
-    for (uint32_t i = tid; i < cap; i += kJoinThreads) stab[i] = kEmptySlot;
-    __syncthreads();
-    join_insert(a, bb, bn, stab, cap, kJoinThreads);
-    __syncthreads();
-  }
+  // a persistent block takes a contiguous range of the probe tiles: tiles of one partition
+  // are adjacent, so a block mostly works through whole partitions in order
+  const uint32_t total = a.probe.tile_start[a.probe.count];
+  const uint32_t t0 = static_cast<uint32_t>((static_cast<uint64_t>(total) * blockIdx.x) / gridDim.x);
+  const uint32_t t1 = static_cast<uint32_t>((static_cast<uint64_t>(total) * (blockIdx.x + 1)) / gridDim.x);
   uint64_t sum = 0, matches = 0;
-#pragma unroll
-  for (int i = 0; i < kJoinItems; ++i) {
-    if (i * kJoinThreads + tid >= valid) continue;
-    uint32_t h = slot_hash(k[i]) & mask;
-    for (uint32_t step = 0; step < cap; ++step) {
-      const uint64_t s = table[h];
-      if (s == kEmptySlot) break;
-      if (static_cast<uint32_t>(s) == static_cast<uint32_t>(k[i])) {
-        sum += static_cast<uint64_t>(static_cast<int64_t>(pay[i]) * static_cast<int64_t>(static_cast<int32_t>(s >> 32)));
-        matches += 1;
-        break;
+  int built = -1;  // partition whose table is in shared memory
+  for (uint32_t b = t0; b < t1; ++b) {
+    const TileAt at = find_tile(a.probe, b, kJoinTile);
+    const int p = at.seg;
+    const int64_t bb = a.b_begin[p];
+    const uint32_t bn = a.b_count[p];
+    const uint32_t cap = join_capacity(bn);
+    const bool in_smem = cap <= static_cast<uint32_t>(kJoinSlots);
+    if (tid == 0 && b + 1 < t1) {  // the next tile's rows travel to L2 meanwhile
+      const TileAt nx = find_tile(a.probe, b + 1, kJoinTile);
+      prefetch_rows(a.pkey, nx.row0, nx.valid);
+      prefetch_rows(a.ppay, nx.row0, nx.valid);
+      if (nx.seg != p) {
+        prefetch_rows(a.bkey, a.b_begin[nx.seg], a.b_count[nx.seg]);
+        prefetch_rows(a.bval, a.b_begin[nx.seg], a.b_count[nx.seg]);
       }
-      h = (h + 1) & mask;
+    }
+    const uint64_t* table = in_smem ? stab : a.arena + 4 * bb;  // the arena's table is built already
+    const uint32_t mask = cap - 1;
+    int32_t k[kJoinItems], pay[kJoinItems];
+#pragma unroll
+    for (int i = 0; i < kJoinItems; ++i) {
+      const int idx = i * kJoinThreads + tid;
+      k[i] = idx < at.valid ? a.pkey[at.row0 + idx] : 0;
+      pay[i] = idx < at.valid ? a.ppay[at.row0 + idx] : 0;
+    }
+    if (in_smem && built != p) {
+      __syncthreads();  // the previous partition's probes are done with the table
+      for (uint32_t i = tid; i < cap; i += kJoinThreads) stab[i] = kEmptySlot;
+      __syncthreads();
+      join_insert(a, bb, bn, stab, cap, kJoinThreads);
+      __syncthreads();
+      built = p;
+    }
+#pragma unroll
+    for (int i = 0; i < kJoinItems; ++i) {
+      if (i * kJoinThreads + tid >= at.valid) continue;
+      uint32_t h = slot_hash(k[i]) & mask;
+      for (uint32_t step = 0; step < cap; ++step) {
+        const uint64_t s = table[h];
+        if (s == kEmptySlot) break;
+        if (static_cast<uint32_t>(s) == static_cast<uint32_t>(k[i])) {
+          sum += static_cast<uint64_t>(static_cast<int64_t>(pay[i]) * static_cast<int64_t>(static_cast<int32_t>(s >> 32)));
+          matches += 1;
+          break;
+        }
+        h = (h + 1) & mask;
+      }
     }
   }
   const uint64_t bs = block_sum_u64<kJoinThreads>(sum, red);
@@ -693,7 +717,8 @@ int run_pass(const Level& L, int segments, int64_t n, const int32_t* kin, const 
   if (cudaMemsetAsync(L.hist, 0, static_cast<size_t>(segments) * kBuckets * 4, s) != cudaSuccess) return CRYS_ECUDA;
   Segs S{L.seg_begin, L.seg_size, L.tile_start, L.tile_seg, segments};
   const int64_t grid = tiles_bound(n, segments, kPartTile);
-  part_hist_kernel<<<static_cast<unsigned>(grid), kPartThreads, 0, s>>>(kin, S, f, L.hist);
+  const int64_t hist_grid = grid < static_cast<int64_t>(sm_count()) * 8 ? grid : static_cast<int64_t>(sm_count()) * 8;
+  part_hist_kernel<<<static_cast<unsigned>(hist_grid), kPartThreads, 0, s>>>(kin, S, f, L.hist);
   note_launch();
   part_scan_kernel<<<static_cast<unsigned>(segments), kBuckets, 0, s>>>(L.hist, L.seg_begin, L.cursor,
                                                                         L.bucket_begin);
@@ -899,7 +924,12 @@ extern "C" int crys_join_partitioned(const int32_t* bkeys, const int32_t* bvals,
   note_launch();
   const size_t smem = static_cast<size_t>(kJoinSlots) * 8;
   if (!allow_smem(join_partition_kernel, smem)) return CRYS_ECUDA;
-  const int64_t grid = tiles_bound(np, parts, kJoinTile);
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, join_partition_kernel, kJoinThreads, smem) != cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  int64_t grid = tiles_bound(np, parts, kJoinTile);
+  if (grid > static_cast<int64_t>(per_sm) * sm_count()) grid = static_cast<int64_t>(per_sm) * sm_count();
   join_partition_kernel<<<static_cast<unsigned>(grid), kJoinThreads, smem, s>>>(a);
   note_launch();
   return check_launch();
