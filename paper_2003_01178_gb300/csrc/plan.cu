@@ -286,7 +286,7 @@ __device__ __forceinline__ uint32_t eval_shared(const DevQuery& q, const CachedC
 // tile's columns are already on their way to L2 (bulk prefetch), so every column the
 // query reads is loaded for all rows (no selective loads and no per-group branches);
 // predicates only clear bits of the row bitmap and dead rows contribute 0.
-template <int THREADS, int ITEMS>
+template <int THREADS, int ITEMS, bool SEL = false>
 __device__ __forceinline__ uint32_t eval_eager_loop(const DevQuery& q, const GlobalCols& cols, uint32_t alive,
                                                int32_t (&gid)[ITEMS], int64_t (&val)[ITEMS],
                                                int32_t* err, uint64_t pol_table) {
@@ -335,12 +335,17 @@ __device__ __forceinline__ uint32_t eval_eager_loop(const DevQuery& q, const Glo
       }
     }
   }
+  // the aggregate operands; with SEL a 16-byte group with no live row is not read
+  // (selective load: the Section 5.3 model's later-column term, one line per surviving
+  // row at most), otherwise every group is read and the loads can go out early
 #pragma unroll
   for (int j = 0; j < VEC; ++j) {
     const int p = (j * THREADS + tid) * 4;
-    int32_t va[4], vb[4] = {0, 0, 0, 0};
-    unpack4(cols.load4(q.agg_a, p), va);
-    if (q.agg_op != CRYS_AGG_A) unpack4(cols.load4(q.agg_b, p), vb);
+    int32_t va[4] = {0, 0, 0, 0}, vb[4] = {0, 0, 0, 0};
+    if (!SEL || ((alive >> (4 * j)) & 0xFu)) {
+      unpack4(cols.load4(q.agg_a, p), va);
+      if (q.agg_op != CRYS_AGG_A) unpack4(cols.load4(q.agg_b, p), vb);
+    }
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
       const int64_t x = va[e], y = vb[e];
@@ -514,7 +519,8 @@ struct PlanArgs {
   int64_t row_begin, row_end;
   DevQuery q;
   int32_t* err;
-  uint32_t col_mask;  // fact columns the query reads
+  uint32_t col_mask;   // fact columns the query reads
+  uint32_t late_mask;  // columns read only by the aggregate (selective loads, see plan_kernel)
 };
 
 // Thread 0 asks the copy engine to bring tile `t` of every column in `mask` into L2
@@ -556,9 +562,17 @@ __global__ void __launch_bounds__(THREADS) plan_kernel(const __grid_constant__ P
       const int64_t tt = blockIdx.x + static_cast<int64_t>(d) * gridDim.x;
       if (tt < ntiles) prefetch_tile(a.cols, a.col_mask, a.row_begin, tt, TILE, nrows);
     }
+  // Selective loads of the late columns (read by the aggregate only): every warp counts
+  // the 128-byte lines of those columns its live rows needed (an L2 miss fills a whole
+  // line, so a line is saved only when all its 32 rows failed).  Once fewer than a third
+  // were needed, the warp reads them for live 16-byte groups only, and thread 0 stops
+  // prefetching them into L2 (by warp 0's counts), so their dead lines stay in DRAM.
+  uint32_t need_lines = 0, seen_lines = 0;
   for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const bool sparse = a.late_mask && seen_lines >= 64u && 3u * need_lines < seen_lines;
     const int64_t ahead = t + static_cast<int64_t>(kPrefetchTiles) * gridDim.x;
-    if (threadIdx.x == 0 && ahead < ntiles) prefetch_tile(a.cols, a.col_mask, a.row_begin, ahead, TILE, nrows);
+    if (threadIdx.x == 0 && ahead < ntiles)
+      prefetch_tile(a.cols, sparse ? (a.col_mask & ~a.late_mask) : a.col_mask, a.row_begin, ahead, TILE, nrows);
     GlobalCols cols;
     cols.pol = pol;
     cols.cols = a.cols;
@@ -566,9 +580,24 @@ __global__ void __launch_bounds__(THREADS) plan_kernel(const __grid_constant__ P
     cols.valid = static_cast<int>((nrows - t * TILE) < TILE ? (nrows - t * TILE) : TILE);
     int32_t gid[ITEMS];
     int64_t val[ITEMS];
-    const uint32_t alive = q.never ? 0u
-                                   : eval_eager<THREADS, ITEMS, PRELOAD>(q, cols, rows_present<THREADS, ITEMS>(cols.valid),
-                                                                gid, val, a.err, pol_table);
+    uint32_t alive = 0;
+    if (!q.never) {
+      const uint32_t present = rows_present<THREADS, ITEMS>(cols.valid);
+      if (PRELOAD || !sparse)
+        alive = eval_eager<THREADS, ITEMS, PRELOAD>(q, cols, present, gid, val, a.err, pol_table);
+      else
+        alive = eval_eager_loop<THREADS, ITEMS, true>(q, cols, present, gid, val, a.err, pol_table);
+    }
+    if (!PRELOAD && a.late_mask) {
+#pragma unroll
+      for (int j = 0; j < ITEMS / 4; ++j) {
+        // lanes 8m .. 8m+7 read the 16-byte groups of 128-byte line m of the warp's 512 bytes
+        const uint32_t b = __ballot_sync(0xFFFFFFFFu, ((alive >> (4 * j)) & 0xFu) != 0u);
+        need_lines += static_cast<uint32_t>((b & 0xFFu) != 0) + ((b & 0xFF00u) != 0) + ((b & 0xFF0000u) != 0) +
+                      ((b & 0xFF000000u) != 0);
+        seen_lines += 4u;
+      }
+    }
     if (q.acc_mode == kAccSingle) {
 #pragma unroll
       for (int i = 0; i < ITEMS; ++i) my_sum += static_cast<uint64_t>(val[i]);
@@ -1759,6 +1788,15 @@ int crys_run_plan(const crys_table* fact, const crys_plan* plan, crys_stream str
   if (to_device(*fact, *plan, &a.q, &mask) != CRYS_OK) return CRYS_EINVAL;
   for (int c = 0; c < fact->n_cols; ++c) a.cols[c] = fact->cols[c];
   a.col_mask = mask;
+  // columns only the aggregate reads, when a filter runs before it (a fact predicate or a
+  // join): candidates for selective loads
+  a.late_mask = 0;
+  if (a.q.n_preds > 0 || a.q.n_joins > 0) {
+    uint32_t early = 0;
+    for (int f = 0; f < a.q.n_preds; ++f) early |= 1u << a.q.pred_col[f];
+    for (int j = 0; j < a.q.n_joins; ++j) early |= 1u << a.q.joins[j].fk_col;
+    a.late_mask = ((1u << a.q.agg_a) | (1u << a.q.agg_b)) & ~early;
+  }
   a.row_begin = 0;
   a.row_end = fact->n_rows;
   a.err = device_error_word();

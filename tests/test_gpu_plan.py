@@ -52,6 +52,28 @@ def test_q1_parity(crys, orc, n, variant, kind):
     crys.crys_set_tile(crys.OP_PLAN, 0)
 
 
+@pytest.mark.parametrize("variant", range(4))
+def test_selective_aggregate_loads(crys, orc, variant):
+    """Filters that keep very few rows: the aggregate column is read only for the 16-byte
+    groups with a live row (and stops being prefetched); sums stay exact."""
+    crys.crys_set_tile(crys.OP_PLAN, variant)
+    n = 3_000_017
+    host = datagen.q1_tables(55, n)
+    fact = {k: _dev(v) for k, v in host["fact"].items()}
+    dim = {k: _dev(v) for k, v in host["dim"].items()}
+    ht = crys.HashTable.build(dim["key"], dim["yr"], filters=[(dim["yr"], 3, 3)])
+    cols = [fact["fk"], fact["a"], fact["b"], fact["c"]]
+    hcols = [host["fact"][k] for k in ("fk", "a", "b", "c")]
+    ojoin = [{"fk_col": 0, "keys": host["dim"]["key"], "preds": [(host["dim"]["yr"], 3, 3)], "group": None,
+              "card": 1}]
+    for preds, agg in [([(1, 1, 1), (2, 1, 3)], ("mul", 3, 2)), ([(1, 50, 50)], ("sum", 3, None)),
+                       ([], ("sub", 3, 1)), ([(2, 10, 10)], ("add", 3, 3))]:
+        sums, counts = crys.run_plan(cols, preds, [(0, ht, 0)], agg)
+        rs, rc = orc.run_plan_raw(hcols, preds, ojoin, agg)
+        assert int(sums[0].item()) == int(rs[0]) and int(counts[0].item()) == int(rc[0]), (preds, agg)
+    crys.crys_set_tile(crys.OP_PLAN, 0)
+
+
 def test_q1_year_invariant_on_gpu(crys, orc):
     host = datagen.q1_tables(77, 1 << 20)
     fact = {k: _dev(v) for k, v in host["fact"].items()}
