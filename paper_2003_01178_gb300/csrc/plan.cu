@@ -363,62 +363,72 @@ __device__ __forceinline__ uint32_t eval_eager_loop(const DevQuery& q, const Glo
 }
 
 // The same evaluation with every column load of the tile issued before any value is
-// used (up to two fact predicates, up to four joins' foreign keys and the aggregate
+// used (up to two fact predicates, up to two joins' foreign keys and the aggregate
 // operands), so that one L2 round trip serves the tile instead of one per step; for
-// tiles of at most 4 rows per thread, where the loaded vectors fit in registers.
+// tiles of 4 or 8 rows per thread, where the loaded vectors fit in registers.
 template <int THREADS, int ITEMS>
 __device__ __forceinline__ uint32_t eval_eager_preload(const DevQuery& q, const GlobalCols& cols, uint32_t alive,
                                                        int32_t (&gid)[ITEMS], int64_t (&val)[ITEMS],
                                                        int32_t* err, uint64_t pol_table) {
-  static_assert(ITEMS == 4, "one 16-byte vector per column and thread");
-  constexpr int KP = 2;
-  const int p = static_cast<int>(threadIdx.x) * 4;
-  int4 pv[KP], kv[CRYS_MAX_JOINS];
+  static_assert(ITEMS == 4 || ITEMS == 8, "one or two 16-byte vectors per column and thread");
+  constexpr int VEC = ITEMS / 4;
+  constexpr int KP = 2;  // fact predicates whose columns go out up front
+  constexpr int KJ = 2;  // joins whose keys go out up front
+  const int tid = static_cast<int>(threadIdx.x);
+  int4 pv[KP][VEC], kv[KJ][VEC], av[VEC], bv[VEC];
 #pragma unroll
-  for (int f = 0; f < KP; ++f) pv[f] = f < q.n_preds ? cols.load4(q.pred_col[f], p) : make_int4(0, 0, 0, 0);
+  for (int j = 0; j < VEC; ++j) {
+    const int p = (j * THREADS + tid) * 4;
 #pragma unroll
-  for (int jn = 0; jn < CRYS_MAX_JOINS; ++jn)
-    kv[jn] = jn < q.n_joins ? cols.load4(q.joins[jn].fk_col, p) : make_int4(0, 0, 0, 0);
-  const int4 av = cols.load4(q.agg_a, p);
-  const int4 bv = q.agg_op != CRYS_AGG_A ? cols.load4(q.agg_b, p) : make_int4(0, 0, 0, 0);
+    for (int f = 0; f < KP; ++f) pv[f][j] = f < q.n_preds ? cols.load4(q.pred_col[f], p) : make_int4(0, 0, 0, 0);
+#pragma unroll
+    for (int jn = 0; jn < KJ; ++jn) kv[jn][j] = jn < q.n_joins ? cols.load4(q.joins[jn].fk_col, p) : make_int4(0, 0, 0, 0);
+    av[j] = cols.load4(q.agg_a, p);
+    bv[j] = q.agg_op != CRYS_AGG_A ? cols.load4(q.agg_b, p) : make_int4(0, 0, 0, 0);
+  }
+  auto pred = [&](const int32_t (&v)[ITEMS], int32_t lo, uint32_t span) {
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) alive &= ~(static_cast<uint32_t>(!in_span(v[i], lo, span)) << i);
+  };
 #pragma unroll
   for (int f = 0; f < KP; ++f) {
     if (f >= q.n_preds) break;
-    int32_t v[4];
-    unpack4(pv[f], v);
-    const int32_t lo = q.pred_lo[f];
-    const uint32_t span = q.pred_span[f];
+    int32_t v[ITEMS];
 #pragma unroll
-    for (int e = 0; e < 4; ++e) alive &= ~(static_cast<uint32_t>(!in_span(v[e], lo, span)) << e);
+    for (int j = 0; j < VEC; ++j) unpack4(pv[f][j], v + 4 * j);
+    pred(v, q.pred_lo[f], q.pred_span[f]);
   }
   for (int f = KP; f < q.n_preds; ++f) {
-    int32_t v[4];
-    unpack4(cols.load4(q.pred_col[f], p), v);
-    const int32_t lo = q.pred_lo[f];
-    const uint32_t span = q.pred_span[f];
+    int32_t v[ITEMS];
 #pragma unroll
-    for (int e = 0; e < 4; ++e) alive &= ~(static_cast<uint32_t>(!in_span(v[e], lo, span)) << e);
+    for (int j = 0; j < VEC; ++j) unpack4(cols.load4(q.pred_col[f], (j * THREADS + tid) * 4), v + 4 * j);
+    pred(v, q.pred_lo[f], q.pred_span[f]);
   }
 #pragma unroll
-  for (int i = 0; i < 4; ++i) gid[i] = 0;
+  for (int i = 0; i < ITEMS; ++i) gid[i] = 0;
 #pragma unroll
   for (int jn = 0; jn < CRYS_MAX_JOINS; ++jn) {
     if (jn >= q.n_joins) break;
     const DevJoin& J = q.joins[jn];
-    int32_t key[4], value[4];
-    unpack4(kv[jn], key);
-    alive &= probe_items<4>(J.slots, J.hash, key, alive, value, pol_table);
+    int32_t key[ITEMS], value[ITEMS];
+#pragma unroll
+    for (int j = 0; j < VEC; ++j) {
+      if (jn < KJ) unpack4(kv[jn < KJ ? jn : 0][j], key + 4 * j);
+      else unpack4(cols.load4(J.fk_col, (j * THREADS + tid) * 4), key + 4 * j);
+    }
+    alive &= probe_items<ITEMS>(J.slots, J.hash, key, alive, value, pol_table);
     for (int f = 0; f < J.n_fp; ++f) {
       const uint32_t sh = J.fp_shift[f], mk = J.fp_mask[f], span = J.fp_span[f];
       const int32_t lo = J.fp_lo[f];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) alive &= ~(static_cast<uint32_t>(!in_span(field_of(value[i], sh, mk), lo, span)) << i);
+      for (int i = 0; i < ITEMS; ++i)
+        alive &= ~(static_cast<uint32_t>(!in_span(field_of(value[i], sh, mk), lo, span)) << i);
     }
     if (J.card > 0) {
       const uint32_t card = static_cast<uint32_t>(J.card);
       uint32_t bad = 0;
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
+      for (int i = 0; i < ITEMS; ++i) {
         const uint32_t code = static_cast<uint32_t>(field_of(value[i], J.gshift, J.gmask));
         bad |= static_cast<uint32_t>(code >= card) << i;
         gid[i] += static_cast<int32_t>(code) * J.stride;
@@ -430,20 +440,23 @@ __device__ __forceinline__ uint32_t eval_eager_preload(const DevQuery& q, const 
       }
     }
   }
-  int32_t va[4], vb[4];
-  unpack4(av, va);
-  unpack4(bv, vb);
 #pragma unroll
-  for (int e = 0; e < 4; ++e) {
-    const int64_t x = va[e], y = vb[e];
-    int64_t r;
-    switch (q.agg_op) {
-      case CRYS_AGG_A_MUL_B: r = x * y; break;
-      case CRYS_AGG_A_SUB_B: r = x - y; break;
-      case CRYS_AGG_A_ADD_B: r = x + y; break;
-      default: r = x; break;
+  for (int j = 0; j < VEC; ++j) {
+    int32_t va[4], vb[4];
+    unpack4(av[j], va);
+    unpack4(bv[j], vb);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int64_t x = va[e], y = vb[e];
+      int64_t r;
+      switch (q.agg_op) {
+        case CRYS_AGG_A_MUL_B: r = x * y; break;
+        case CRYS_AGG_A_SUB_B: r = x - y; break;
+        case CRYS_AGG_A_ADD_B: r = x + y; break;
+        default: r = x; break;
+      }
+      val[4 * j + e] = ((alive >> (4 * j + e)) & 1u) ? r : 0;
     }
-    val[e] = ((alive >> e) & 1u) ? r : 0;
   }
   return alive;
 }
@@ -452,7 +465,7 @@ template <int THREADS, int ITEMS, bool PRELOAD>
 __device__ __forceinline__ uint32_t eval_eager(const DevQuery& q, const GlobalCols& cols, uint32_t alive,
                                                int32_t (&gid)[ITEMS], int64_t (&val)[ITEMS],
                                                int32_t* err, uint64_t pol_table) {
-  if constexpr (PRELOAD && ITEMS == 4) {
+  if constexpr (PRELOAD && (ITEMS == 4 || ITEMS == 8)) {
     return eval_eager_preload<THREADS, ITEMS>(q, cols, alive, gid, val, err, pol_table);
   } else {
     return eval_eager_loop<THREADS, ITEMS>(q, cols, alive, gid, val, err, pol_table);
@@ -1368,13 +1381,13 @@ int launch_plan(PlanArgs& a, cudaStream_t s) {
     a.q.acc_mode = kAccGlobal;
   }
   // With few tiles per block the kernel waits on each tile's loads in turn: then all of
-  // a tile's loads go out together (4-row tiles only); with many tiles per block the
+  // a tile's loads go out together (4- and 8-row items); with many tiles per block the
   // lighter looping evaluation keeps more blocks resident.
   const int64_t ntiles = (a.row_end - a.row_begin + TILE - 1) / TILE;
   auto kl = plan_kernel<THREADS, ITEMS, false>;
   if (!allow_smem(kl, smem)) return CRYS_ECUDA;
   int grid = persistent_grid(kl, THREADS, smem, ntiles);
-  const bool preload = ITEMS == 4 && ntiles <= 8 * static_cast<int64_t>(grid);
+  const bool preload = (ITEMS == 4 || ITEMS == 8) && ntiles <= 8 * static_cast<int64_t>(grid);
   auto k = preload ? plan_kernel<THREADS, ITEMS, true> : kl;
   if (preload) {
     if (!allow_smem(k, smem)) return CRYS_ECUDA;
