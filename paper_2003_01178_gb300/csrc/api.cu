@@ -72,6 +72,35 @@ bool set_dynamic_smem(const void* kernel, size_t bytes) {
   return true;
 }
 
+int blocks_per_sm(const void* kernel, int threads, size_t smem) {
+  struct Key {
+    const void* kernel;
+    int threads;
+    size_t smem;
+    bool operator==(const Key& o) const { return kernel == o.kernel && threads == o.threads && smem == o.smem; }
+  };
+  struct KeyHash {
+    size_t operator()(const Key& k) const {
+      return std::hash<const void*>()(k.kernel) ^ (static_cast<size_t>(k.threads) << 1) ^ (k.smem << 12);
+    }
+  };
+  static std::mutex m;
+  static std::unordered_map<Key, int, KeyHash> known[kMaxDevices];
+  const int dev = current_device();
+  const Key key{kernel, threads, smem};
+  {
+    std::lock_guard<std::mutex> lock(m);
+    auto it = known[dev].find(key);
+    if (it != known[dev].end()) return it->second;
+  }
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess || per_sm < 1)
+    per_sm = 1;
+  std::lock_guard<std::mutex> lock(m);
+  known[dev][key] = per_sm;
+  return per_sm;
+}
+
 bool take_stall(int op, uint32_t* first_tile, uint64_t* wait_ns) {
   std::lock_guard<std::mutex> lock(g_stall_mutex);
   *first_tile = 0;

@@ -49,15 +49,15 @@ inline int stages_for(size_t stage_bytes, size_t extra_bytes, int blocks_per_sm)
   return static_cast<int>(s);
 }
 
-// Persistent grid: resident blocks per SM (from the occupancy calculator) x SMs,
-// capped by the number of tiles.
+// Resident blocks per SM of a kernel launched with `threads` threads and `smem` bytes of
+// dynamic shared memory (the occupancy calculator), at least 1; remembered per device,
+// kernel and launch shape, since a short launch cannot afford the query every time.
+int blocks_per_sm(const void* kernel, int threads, size_t smem);
+
+// Persistent grid: resident blocks per SM x SMs, capped by the number of tiles.
 template <typename K>
 int persistent_grid(K kernel, int threads, size_t smem, int64_t tiles) {
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) !=
-          cudaSuccess ||
-      per_sm < 1)
-    per_sm = 1;
+  const int per_sm = blocks_per_sm(reinterpret_cast<const void*>(kernel), threads, smem);
   int64_t g = static_cast<int64_t>(per_sm) * sm_count();
   if (tiles < g) g = tiles;
   return g < 1 ? 1 : static_cast<int>(g);

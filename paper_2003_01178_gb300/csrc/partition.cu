@@ -924,10 +924,7 @@ extern "C" int crys_join_partitioned(const int32_t* bkeys, const int32_t* bvals,
   note_launch();
   const size_t smem = static_cast<size_t>(kJoinSlots) * 8;
   if (!allow_smem(join_partition_kernel, smem)) return CRYS_ECUDA;
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, join_partition_kernel, kJoinThreads, smem) != cudaSuccess ||
-      per_sm < 1)
-    per_sm = 1;
+  const int per_sm = blocks_per_sm(reinterpret_cast<const void*>(join_partition_kernel), kJoinThreads, smem);
   int64_t grid = tiles_bound(np, parts, kJoinTile);
   if (grid > static_cast<int64_t>(per_sm) * sm_count()) grid = static_cast<int64_t>(per_sm) * sm_count();
   join_partition_kernel<<<static_cast<unsigned>(grid), kJoinThreads, smem, s>>>(a);

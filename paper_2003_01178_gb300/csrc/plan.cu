@@ -88,6 +88,14 @@ struct GlobalCols {
   }
 };
 
+// Column access for a tile known to be full: every 16-byte group exists.
+struct FullTileCols {
+  const int32_t* const* cols;
+  int64_t row0;
+  uint64_t pol;
+  __device__ __forceinline__ int4 load4(int c, int p) const { return ld_stream_v4(cols[c] + row0 + p, pol); }
+};
+
 // Column loads that stay in L1: the columns a shared scan's queries read for predicates
 // and aggregates are read by several queries of the batch in a row.  In L2 they are the
 // first lines to go: the tile is not read again once its queries are done with it.
@@ -133,6 +141,21 @@ __device__ __forceinline__ uint32_t probe_items(const uint64_t* slots, const Has
                                                 int32_t (&value)[ITEMS], uint64_t pol) {
   uint32_t h[ITEMS];
   uint64_t slot[ITEMS];
+  if (hf.steps == 0u && hf.mult == 1u && hf.shift == 0u && hf.mask == 0xFFFFFFFFu) {
+    // direct table (uniform branch): a key below the capacity is in slot `key` or
+    // absent, one read per row
+    uint32_t found = 0;
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i)
+      slot[i] = ((live >> i) & 1u) && static_cast<uint32_t>(key[i]) < hf.limit ? ld_slot(slots + key[i], pol) : kEmptySlot;
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+      const bool hit = slot[i] != kEmptySlot && static_cast<uint32_t>(slot[i]) == static_cast<uint32_t>(key[i]);
+      value[i] = hit ? static_cast<int32_t>(slot[i] >> 32) : 0;
+      found |= static_cast<uint32_t>(hit) << i;
+    }
+    return found;
+  }
 #pragma unroll
   for (int i = 0; i < ITEMS; ++i) {
     h[i] = hash_slot(key[i], hf);
@@ -362,30 +385,48 @@ __device__ __forceinline__ uint32_t eval_eager_loop(const DevQuery& q, const Glo
   return alive;
 }
 
-// The same evaluation with every column load of the tile issued before any value is
-// used (up to two fact predicates, up to two joins' foreign keys and the aggregate
-// operands), so that one L2 round trip serves the tile instead of one per step; for
-// tiles of 4 or 8 rows per thread, where the loaded vectors fit in registers.
-template <int THREADS, int ITEMS>
-__device__ __forceinline__ uint32_t eval_eager_preload(const DevQuery& q, const GlobalCols& cols, uint32_t alive,
-                                                       int32_t (&gid)[ITEMS], int64_t (&val)[ITEMS],
-                                                       int32_t* err, uint64_t pol_table) {
-  static_assert(ITEMS == 4 || ITEMS == 8, "one or two 16-byte vectors per column and thread");
-  constexpr int VEC = ITEMS / 4;
-  constexpr int KP = 2;  // fact predicates whose columns go out up front
-  constexpr int KJ = 2;  // joins whose keys go out up front
-  const int tid = static_cast<int>(threadIdx.x);
+// The column vectors of one tile that go out before any is used: up to two fact
+// predicates, up to two joins' foreign keys and the aggregate operands.
+template <int ITEMS>
+struct TileVectors {
+  static constexpr int VEC = ITEMS / 4;
+  static constexpr int KP = 2;  // fact predicates whose columns go out up front
+  static constexpr int KJ = 2;  // joins whose keys go out up front
   int4 pv[KP][VEC], kv[KJ][VEC], av[VEC], bv[VEC];
+};
+
+template <int THREADS, int ITEMS, typename Cols>
+__device__ __forceinline__ void load_tile_vectors(const DevQuery& q, const Cols& cols, TileVectors<ITEMS>& r) {
+  using R = TileVectors<ITEMS>;
+  const int tid = static_cast<int>(threadIdx.x);
 #pragma unroll
-  for (int j = 0; j < VEC; ++j) {
+  for (int j = 0; j < R::VEC; ++j) {
     const int p = (j * THREADS + tid) * 4;
 #pragma unroll
-    for (int f = 0; f < KP; ++f) pv[f][j] = f < q.n_preds ? cols.load4(q.pred_col[f], p) : make_int4(0, 0, 0, 0);
+    for (int f = 0; f < R::KP; ++f) r.pv[f][j] = f < q.n_preds ? cols.load4(q.pred_col[f], p) : make_int4(0, 0, 0, 0);
 #pragma unroll
-    for (int jn = 0; jn < KJ; ++jn) kv[jn][j] = jn < q.n_joins ? cols.load4(q.joins[jn].fk_col, p) : make_int4(0, 0, 0, 0);
-    av[j] = cols.load4(q.agg_a, p);
-    bv[j] = q.agg_op != CRYS_AGG_A ? cols.load4(q.agg_b, p) : make_int4(0, 0, 0, 0);
+    for (int jn = 0; jn < R::KJ; ++jn)
+      r.kv[jn][j] = jn < q.n_joins ? cols.load4(q.joins[jn].fk_col, p) : make_int4(0, 0, 0, 0);
+    r.av[j] = cols.load4(q.agg_a, p);
+    r.bv[j] = q.agg_op != CRYS_AGG_A ? cols.load4(q.agg_b, p) : make_int4(0, 0, 0, 0);
   }
+}
+
+// Evaluation of a tile whose leading column vectors are already in registers.
+template <int THREADS, int ITEMS, typename Cols>
+__device__ __forceinline__ uint32_t eval_tile_vectors(const DevQuery& q, const Cols& cols,
+                                                      const TileVectors<ITEMS>& tv, uint32_t alive,
+                                                      int32_t (&gid)[ITEMS], int64_t (&val)[ITEMS],
+                                                      int32_t* err, uint64_t pol_table) {
+  static_assert(ITEMS == 4 || ITEMS == 8, "one or two 16-byte vectors per column and thread");
+  constexpr int VEC = ITEMS / 4;
+  constexpr int KP = TileVectors<ITEMS>::KP;
+  constexpr int KJ = TileVectors<ITEMS>::KJ;
+  const int tid = static_cast<int>(threadIdx.x);
+  const auto& pv = tv.pv;
+  const auto& kv = tv.kv;
+  const auto& av = tv.av;
+  const auto& bv = tv.bv;
   auto pred = [&](const int32_t (&v)[ITEMS], int32_t lo, uint32_t span) {
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) alive &= ~(static_cast<uint32_t>(!in_span(v[i], lo, span)) << i);
@@ -461,6 +502,18 @@ __device__ __forceinline__ uint32_t eval_eager_preload(const DevQuery& q, const 
   return alive;
 }
 
+// The same evaluation with every leading column load of the tile issued before any value
+// is used, so that one L2 round trip serves the tile instead of one per step; for tiles
+// of 4 or 8 rows per thread, where the loaded vectors fit in registers.
+template <int THREADS, int ITEMS>
+__device__ __forceinline__ uint32_t eval_eager_preload(const DevQuery& q, const GlobalCols& cols, uint32_t alive,
+                                                       int32_t (&gid)[ITEMS], int64_t (&val)[ITEMS],
+                                                       int32_t* err, uint64_t pol_table) {
+  TileVectors<ITEMS> r;
+  load_tile_vectors<THREADS, ITEMS>(q, cols, r);
+  return eval_tile_vectors<THREADS, ITEMS>(q, cols, r, alive, gid, val, err, pol_table);
+}
+
 template <int THREADS, int ITEMS, bool PRELOAD>
 __device__ __forceinline__ uint32_t eval_eager(const DevQuery& q, const GlobalCols& cols, uint32_t alive,
                                                int32_t (&gid)[ITEMS], int64_t (&val)[ITEMS],
@@ -527,6 +580,23 @@ __device__ __forceinline__ void flush_shared(const SharedAcc& acc, int first, in
 
 // ------------------------------------------------------------------ one query
 
+// Programmatic dependent launch: the query kernel is launched while the kernel that
+// clears its outputs still runs, and waits for that kernel (its completion and its
+// stores) only where it first touches the outputs; without a programmatic launch the
+// wait returns at once.
+__device__ __forceinline__ void wait_for_prerequisite_grid() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// Clears a query's sums and counts; lets the dependent query kernel start right away.
+__global__ void __launch_bounds__(256) zero_outputs_kernel(unsigned long long* sums, unsigned long long* counts,
+                                                           int64_t groups) {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  for (int64_t g = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; g < groups; g += stride) {
+    sums[g] = 0;
+    if (counts) counts[g] = 0;
+  }
+}
+
 struct PlanArgs {
   const int32_t* cols[CRYS_MAX_COLS];
   int64_t row_begin, row_end;
@@ -568,6 +638,7 @@ __global__ void __launch_bounds__(THREADS) plan_kernel(const __grid_constant__ P
   const int64_t nrows = a.row_end - a.row_begin;
   const int64_t ntiles = (nrows + TILE - 1) / TILE;
   uint64_t my_sum = 0, my_count = 0;
+  if (q.acc_mode == kAccGlobal) wait_for_prerequisite_grid();  // adds go to the outputs from the first tile on
   const uint64_t pol = policy_evict_first();
   const uint64_t pol_table = policy_evict_last();
   if (threadIdx.x == 0)
@@ -580,44 +651,23 @@ __global__ void __launch_bounds__(THREADS) plan_kernel(const __grid_constant__ P
   // line, so a line is saved only when all its 32 rows failed).  Once fewer than a third
   // were needed, the warp reads them for live 16-byte groups only, and thread 0 stops
   // prefetching them into L2 (by warp 0's counts), so their dead lines stay in DRAM.
-  uint32_t need_lines = 0, seen_lines = 0;
-  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const bool sparse = a.late_mask && seen_lines >= 64u && 3u * need_lines < seen_lines;
-    const int64_t ahead = t + static_cast<int64_t>(kPrefetchTiles) * gridDim.x;
-    if (threadIdx.x == 0 && ahead < ntiles)
-      prefetch_tile(a.cols, sparse ? (a.col_mask & ~a.late_mask) : a.col_mask, a.row_begin, ahead, TILE, nrows);
-    GlobalCols cols;
-    cols.pol = pol;
-    cols.cols = a.cols;
-    cols.row0 = a.row_begin + t * TILE;
-    cols.valid = static_cast<int>((nrows - t * TILE) < TILE ? (nrows - t * TILE) : TILE);
-    int32_t gid[ITEMS];
-    int64_t val[ITEMS];
-    uint32_t alive = 0;
-    if (!q.never) {
-      const uint32_t present = rows_present<THREADS, ITEMS>(cols.valid);
-      if (PRELOAD || !sparse)
-        alive = eval_eager<THREADS, ITEMS, PRELOAD>(q, cols, present, gid, val, a.err, pol_table);
-      else
-        alive = eval_eager_loop<THREADS, ITEMS, true>(q, cols, present, gid, val, a.err, pol_table);
-    }
-    if (!PRELOAD && a.late_mask) {
-#pragma unroll
-      for (int j = 0; j < ITEMS / 4; ++j) {
-        // lanes 8m .. 8m+7 read the 16-byte groups of 128-byte line m of the warp's 512 bytes
-        const uint32_t b = __ballot_sync(0xFFFFFFFFu, ((alive >> (4 * j)) & 0xFu) != 0u);
-        need_lines += static_cast<uint32_t>((b & 0xFFu) != 0) + ((b & 0xFF00u) != 0) + ((b & 0xFF0000u) != 0) +
-                      ((b & 0xFF000000u) != 0);
-        seen_lines += 4u;
-      }
-    }
+  auto tile_cols = [&](int64_t t) {
+    GlobalCols c;
+    c.pol = pol;
+    c.cols = a.cols;
+    c.row0 = a.row_begin + t * TILE;
+    c.valid = static_cast<int>((nrows - t * TILE) < TILE ? (nrows - t * TILE) : TILE);
+    return c;
+  };
+  // BlockAggregate of one tile's rows into this thread's sums or the accumulators
+  auto accumulate = [&](uint32_t alive, const int32_t (&gid)[ITEMS], const int64_t (&val)[ITEMS]) {
     if (q.acc_mode == kAccSingle) {
 #pragma unroll
       for (int i = 0; i < ITEMS; ++i) my_sum += static_cast<uint64_t>(val[i]);
       my_count += __popc(alive);
-      continue;
+      return;
     }
-    if (!alive) continue;
+    if (!alive) return;
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
       if (!((alive >> i) & 1u)) continue;
@@ -629,16 +679,91 @@ __global__ void __launch_bounds__(THREADS) plan_kernel(const __grid_constant__ P
         if (q.counts) red_add_global(q.counts + gid[i], 1ull, pol_table);
       }
     }
+  };
+  if constexpr (PRELOAD && ITEMS == 4) {
+    // Few tiles per block: a software pipeline.  The next tile's leading column vectors
+    // are loaded into registers before this tile is evaluated, so that their latency
+    // overlaps the evaluation instead of every warp of the SM waiting on its loads and
+    // then computing in step with the others.
+    // Full tiles (all but possibly the last) load without per-group bounds tests.
+    auto full_cols = [&](const GlobalCols& c) { return FullTileCols{c.cols, c.row0, c.pol}; };
+    auto load = [&](int64_t tt, TileVectors<ITEMS>& r) {
+      const GlobalCols c = tile_cols(tt);
+      if (c.valid == TILE)
+        load_tile_vectors<THREADS, ITEMS>(q, full_cols(c), r);
+      else
+        load_tile_vectors<THREADS, ITEMS>(q, c, r);
+    };
+    TileVectors<ITEMS> cur, nxt;
+    int64_t t = blockIdx.x;
+    if (t < ntiles && !q.never) load(t, cur);
+    for (; t < ntiles; t += gridDim.x) {
+      const int64_t ahead = t + static_cast<int64_t>(kPrefetchTiles) * gridDim.x;
+      if (threadIdx.x == 0 && ahead < ntiles) prefetch_tile(a.cols, a.col_mask, a.row_begin, ahead, TILE, nrows);
+      const GlobalCols cols = tile_cols(t);
+      const int64_t tn = t + gridDim.x;
+      if (tn < ntiles && !q.never) load(tn, nxt);
+      int32_t gid[ITEMS];
+      int64_t val[ITEMS];
+#pragma unroll
+      for (int i = 0; i < ITEMS; ++i) {
+        gid[i] = 0;
+        val[i] = 0;
+      }
+      uint32_t alive = 0;
+      if (!q.never) {
+        if (cols.valid == TILE)
+          alive = eval_tile_vectors<THREADS, ITEMS>(q, full_cols(cols), cur, (1u << ITEMS) - 1u, gid, val, a.err,
+                                                    pol_table);
+        else
+          alive = eval_tile_vectors<THREADS, ITEMS>(q, cols, cur, rows_present<THREADS, ITEMS>(cols.valid), gid, val,
+                                                    a.err, pol_table);
+      }
+      accumulate(alive, gid, val);
+      cur = nxt;
+    }
+  } else {
+    uint32_t need_lines = 0, seen_lines = 0;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+      const bool sparse = a.late_mask && seen_lines >= 64u && 3u * need_lines < seen_lines;
+      const int64_t ahead = t + static_cast<int64_t>(kPrefetchTiles) * gridDim.x;
+      if (threadIdx.x == 0 && ahead < ntiles)
+        prefetch_tile(a.cols, sparse ? (a.col_mask & ~a.late_mask) : a.col_mask, a.row_begin, ahead, TILE, nrows);
+      const GlobalCols cols = tile_cols(t);
+      int32_t gid[ITEMS];
+      int64_t val[ITEMS];
+      uint32_t alive = 0;
+      if (!q.never) {
+        const uint32_t present = rows_present<THREADS, ITEMS>(cols.valid);
+        if (PRELOAD || !sparse)
+          alive = eval_eager<THREADS, ITEMS, PRELOAD>(q, cols, present, gid, val, a.err, pol_table);
+        else
+          alive = eval_eager_loop<THREADS, ITEMS, true>(q, cols, present, gid, val, a.err, pol_table);
+      }
+      if (!PRELOAD && a.late_mask) {
+#pragma unroll
+        for (int j = 0; j < ITEMS / 4; ++j) {
+          // lanes 8m .. 8m+7 read the 16-byte groups of 128-byte line m of the warp's 512 bytes
+          const uint32_t b = __ballot_sync(0xFFFFFFFFu, ((alive >> (4 * j)) & 0xFu) != 0u);
+          need_lines += static_cast<uint32_t>((b & 0xFFu) != 0) + ((b & 0xFF00u) != 0) + ((b & 0xFF0000u) != 0) +
+                        ((b & 0xFF000000u) != 0);
+          seen_lines += 4u;
+        }
+      }
+      accumulate(alive, gid, val);
+    }
   }
   if (q.acc_mode == kAccSingle) {
     const uint64_t s = block_sum_u64<THREADS>(my_sum, red);
     const uint64_t c = block_sum_u64<THREADS>(my_count, red);
     if (threadIdx.x == 0 && c) {
+      wait_for_prerequisite_grid();
       atomicAdd(q.sums, static_cast<unsigned long long>(s));
       if (q.counts) atomicAdd(q.counts, static_cast<unsigned long long>(c));
     }
   } else if (q.acc_mode == kAccShared) {
     __syncthreads();
+    wait_for_prerequisite_grid();
     flush_shared<THREADS>(acc, 0, q.groups, q.sums, q.counts);
   }
 }
@@ -1394,7 +1519,18 @@ int launch_plan(PlanArgs& a, cudaStream_t s) {
     grid = persistent_grid(k, THREADS, smem, ntiles);
   }
   if (!counts_fit(a.row_end - a.row_begin, grid)) return CRYS_EINVAL;
-  k<<<grid, THREADS, smem, s>>>(a);
+  // launched while zero_outputs_kernel (issued just before on this stream) still runs
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(static_cast<unsigned>(grid));
+  cfg.blockDim = dim3(THREADS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (cudaLaunchKernelEx(&cfg, k, a) != cudaSuccess) return CRYS_ECUDA;
   note_launch();
   return check_launch();
 }
@@ -1815,7 +1951,14 @@ int crys_run_plan(const crys_table* fact, const crys_plan* plan, crys_stream str
   a.err = device_error_word();
   if (!a.err) return CRYS_ECUDA;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  if (zero_outputs(a.q, s) != CRYS_OK) return CRYS_ECUDA;
+  {
+    const int64_t zb = a.q.groups > 256 ? (a.q.groups + 255) / 256 : 1;
+    const int64_t zcap = static_cast<int64_t>(sm_count()) * 4;
+    zero_outputs_kernel<<<static_cast<unsigned>(zb < zcap ? zb : zcap), 256, 0, s>>>(a.q.sums, a.q.counts,
+                                                                                      a.q.groups);
+    note_launch();
+    if (check_launch() != CRYS_OK) return CRYS_ECUDA;
+  }
   if (fact->n_rows == 0) return CRYS_OK;
   constexpr int kOp = CRYS_OP_PLAN;
   switch (tile_variant(kOp)) {
