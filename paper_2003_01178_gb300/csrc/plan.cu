@@ -768,6 +768,128 @@ __global__ void __launch_bounds__(THREADS) plan_kernel(const __grid_constant__ P
   }
 }
 
+// ------------------------------------------------------------------ one query, fixed shape
+//
+// Plans of the Q1 family (Section 5.3's query 1.x: one or two fact predicates, one join on
+// a direct dimension table with its field predicates, one output group, SUM(a * b) or
+// SUM(a)) compiled for their shape: no loops over plan fields, no switch on the aggregate,
+// full tiles without bounds tests, and the next tile's column vectors in flight while the
+// current one is evaluated.  Used where a block takes few tiles (the launch is short and
+// per-tile overhead shows); other plans, and long launches, take plan_kernel.
+template <int THREADS, int ITEMS, int NP, int AGG>
+__global__ void __launch_bounds__(THREADS) plan_fixed_kernel(const __grid_constant__ PlanArgs a) {
+  static_assert(ITEMS == 4 || ITEMS == 8, "one or two 16-byte vectors per column and thread");
+  static_assert(NP >= 1 && NP <= 2, "one or two fact predicates");
+  constexpr int TILE = THREADS * ITEMS;
+  constexpr int VEC = ITEMS / 4;
+  constexpr bool TWO = AGG != CRYS_AGG_A;  // the aggregate reads a second column
+  __shared__ uint64_t red[THREADS / kWarp];
+  const DevQuery& q = a.q;
+  const DevJoin& J = q.joins[0];
+  const int tid = static_cast<int>(threadIdx.x);
+  const int64_t nrows = a.row_end - a.row_begin;
+  const int64_t ntiles = (nrows + TILE - 1) / TILE;
+  const uint64_t pol = policy_evict_first();
+  const uint64_t pol_table = policy_evict_last();
+  const int32_t* pcol[NP];
+#pragma unroll
+  for (int f = 0; f < NP; ++f) pcol[f] = a.cols[q.pred_col[f]] + a.row_begin;
+  const int32_t* kcol = a.cols[J.fk_col] + a.row_begin;
+  const int32_t* xcol = a.cols[q.agg_a] + a.row_begin;
+  const int32_t* ycol = a.cols[TWO ? q.agg_b : q.agg_a] + a.row_begin;
+  struct Vecs {
+    int4 p[NP][VEC], k[VEC], x[VEC], y[VEC];
+  };
+  auto load4 = [&](const int32_t* col, int64_t row0, int p, int valid) -> int4 {
+    if (p + 4 <= valid) return ld_stream_v4(col + row0 + p, pol);
+    int v[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) v[e] = p + e < valid ? ld_stream(col + row0 + p + e, pol) : 0;
+    return make_int4(v[0], v[1], v[2], v[3]);
+  };
+  auto load = [&](int64_t t, Vecs& V) {
+    const int64_t row0 = t * TILE;
+    const int valid = static_cast<int>((nrows - row0) < TILE ? (nrows - row0) : TILE);
+#pragma unroll
+    for (int j = 0; j < VEC; ++j) {
+      const int p = (j * THREADS + tid) * 4;
+      if (valid == TILE) {
+#pragma unroll
+        for (int f = 0; f < NP; ++f) V.p[f][j] = ld_stream_v4(pcol[f] + row0 + p, pol);
+        V.k[j] = ld_stream_v4(kcol + row0 + p, pol);
+        V.x[j] = ld_stream_v4(xcol + row0 + p, pol);
+        if (TWO) V.y[j] = ld_stream_v4(ycol + row0 + p, pol);
+      } else {
+#pragma unroll
+        for (int f = 0; f < NP; ++f) V.p[f][j] = load4(pcol[f], row0, p, valid);
+        V.k[j] = load4(kcol, row0, p, valid);
+        V.x[j] = load4(xcol, row0, p, valid);
+        if (TWO) V.y[j] = load4(ycol, row0, p, valid);
+      }
+    }
+  };
+  uint64_t my_sum = 0, my_count = 0;
+  if (threadIdx.x == 0)
+    for (int d = 0; d < kPrefetchTiles; ++d) {
+      const int64_t tt = blockIdx.x + static_cast<int64_t>(d) * gridDim.x;
+      if (tt < ntiles) prefetch_tile(a.cols, a.col_mask, a.row_begin, tt, TILE, nrows);
+    }
+  Vecs cur, nxt;
+  int64_t t = blockIdx.x;
+  if (t < ntiles && !q.never) load(t, cur);
+  for (; t < ntiles && !q.never; t += gridDim.x) {
+    const int64_t ahead = t + static_cast<int64_t>(kPrefetchTiles) * gridDim.x;
+    if (threadIdx.x == 0 && ahead < ntiles) prefetch_tile(a.cols, a.col_mask, a.row_begin, ahead, TILE, nrows);
+    const int64_t tn = t + gridDim.x;
+    if (tn < ntiles) load(tn, nxt);
+    const int64_t row0 = t * TILE;
+    const int valid = static_cast<int>((nrows - row0) < TILE ? (nrows - row0) : TILE);
+#pragma unroll
+    for (int j = 0; j < VEC; ++j) {
+      const int p = (j * THREADS + tid) * 4;
+      int32_t pv[NP][4], key[4], xv[4], yv[4];
+#pragma unroll
+      for (int f = 0; f < NP; ++f) unpack4(cur.p[f][j], pv[f]);
+      unpack4(cur.k[j], key);
+      unpack4(cur.x[j], xv);
+      if (TWO) unpack4(cur.y[j], yv);
+      // BlockPred, then the probe of the surviving rows, all four slot reads in flight
+      bool ok[4];
+      uint64_t slot[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        ok[e] = p + e < valid;
+#pragma unroll
+        for (int f = 0; f < NP; ++f) ok[e] = ok[e] && in_span(pv[f][e], q.pred_lo[f], q.pred_span[f]);
+        slot[e] = ok[e] && static_cast<uint32_t>(key[e]) < J.hash.limit ? ld_slot(J.slots + key[e], pol_table)
+                                                                        : kEmptySlot;
+      }
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        bool hit = ok[e] && slot[e] != kEmptySlot && static_cast<uint32_t>(slot[e]) == static_cast<uint32_t>(key[e]);
+        const int32_t v = static_cast<int32_t>(slot[e] >> 32);
+        for (int f = 0; f < J.n_fp; ++f)
+          hit = hit && in_span(field_of(v, J.fp_shift[f], J.fp_mask[f]), J.fp_lo[f], J.fp_span[f]);
+        int64_t r;
+        if (AGG == CRYS_AGG_A_MUL_B) r = static_cast<int64_t>(xv[e]) * yv[e];
+        else if (AGG == CRYS_AGG_A_SUB_B) r = static_cast<int64_t>(xv[e]) - yv[e];
+        else if (AGG == CRYS_AGG_A_ADD_B) r = static_cast<int64_t>(xv[e]) + yv[e];
+        else r = xv[e];
+        my_sum += hit ? static_cast<uint64_t>(r) : 0ull;
+        my_count += hit ? 1u : 0u;
+      }
+    }
+    cur = nxt;
+  }
+  const uint64_t s = block_sum_u64<THREADS>(my_sum, red);
+  const uint64_t c = block_sum_u64<THREADS>(my_count, red);
+  if (threadIdx.x == 0 && c) {
+    wait_for_prerequisite_grid();
+    atomicAdd(q.sums, static_cast<unsigned long long>(s));
+    if (q.counts) atomicAdd(q.counts, static_cast<unsigned long long>(c));
+  }
+}
+
 // ------------------------------------------------------------------ shared scan
 
 struct ProbeSpec {
@@ -1517,6 +1639,20 @@ int launch_plan(PlanArgs& a, cudaStream_t s) {
   if (preload) {
     if (!allow_smem(k, smem)) return CRYS_ECUDA;
     grid = persistent_grid(k, THREADS, smem, ntiles);
+  }
+  // a plan of the Q1 family in a short launch: the kernel compiled for its shape
+  const DevJoin& J0 = a.q.joins[0];
+  const bool fixed = preload && a.q.acc_mode == kAccSingle && a.q.n_joins == 1 &&
+                     (a.q.n_preds == 1 || a.q.n_preds == 2) && J0.card <= 0 && J0.hash.steps == 0u &&
+                     J0.hash.mult == 1u && J0.hash.shift == 0u && J0.hash.mask == 0xFFFFFFFFu &&
+                     (a.q.agg_op == CRYS_AGG_A_MUL_B || a.q.agg_op == CRYS_AGG_A);
+  if (fixed) {
+    const bool mul = a.q.agg_op == CRYS_AGG_A_MUL_B;
+    if (a.q.n_preds == 2)
+      k = mul ? plan_fixed_kernel<THREADS, ITEMS, 2, CRYS_AGG_A_MUL_B> : plan_fixed_kernel<THREADS, ITEMS, 2, CRYS_AGG_A>;
+    else
+      k = mul ? plan_fixed_kernel<THREADS, ITEMS, 1, CRYS_AGG_A_MUL_B> : plan_fixed_kernel<THREADS, ITEMS, 1, CRYS_AGG_A>;
+    grid = persistent_grid(k, THREADS, 0, ntiles);
   }
   if (!counts_fit(a.row_end - a.row_begin, grid)) return CRYS_EINVAL;
   // launched while zero_outputs_kernel (issued just before on this stream) still runs

@@ -74,6 +74,32 @@ def test_selective_aggregate_loads(crys, orc, variant):
     crys.crys_set_tile(crys.OP_PLAN, 0)
 
 
+@pytest.mark.parametrize("n", [1, 4099, 1_000_003, (1 << 22) + 5])
+@pytest.mark.parametrize("variant", range(4))
+def test_fixed_shape_plans(crys, orc, n, variant):
+    """Plans of the Q1 family (one or two fact predicates, one join on a direct table with
+    one or two field predicates, one group, SUM(a * b) or SUM(a)) run in the kernel
+    compiled for their shape when a launch is short; exact against the oracle, ragged
+    tails included."""
+    crys.crys_set_tile(crys.OP_PLAN, variant)
+    host = datagen.q1_tables(91 + n % 5, n)
+    keys, yr = host["dim"]["key"], host["dim"]["yr"]
+    mo = (np.arange(keys.size) % 12).astype(np.int32)
+    packed = (yr | (mo << 3)).astype(np.int32)
+    ht = crys.HashTable.build(_dev(keys), _dev(packed), capacity=keys.size, kind=crys.HASH_DIRECT)
+    fact = {k: _dev(v) for k, v in host["fact"].items()}
+    cols = [fact["fk"], fact["a"], fact["b"], fact["c"]]
+    hcols = [host["fact"][k] for k in ("fk", "a", "b", "c")]
+    for fps, opreds in [([(0, 3, 3, 3)], [(yr, 3, 3)]), ([(0, 3, 3, 3), (3, 4, 2, 5)], [(yr, 3, 3), (mo, 2, 5)])]:
+        ojoin = [{"fk_col": 0, "keys": keys, "preds": opreds, "group": None, "card": 1}]
+        for preds, agg in [([(1, I32_MIN, 24), (2, 1, 3)], ("mul", 3, 2)), ([(1, 10, 30)], ("mul", 3, 2)),
+                           ([(2, 1, 3), (1, 5, 5)], ("sum", 3, None)), ([(1, 1, 40)], ("sum", 2, None))]:
+            sums, counts = crys.run_plan(cols, preds, [(0, ht, 0, (0, 0), fps)], agg)
+            rs, rc = orc.run_plan_raw(hcols, preds, ojoin, agg)
+            assert int(sums[0].item()) == int(rs[0]) and int(counts[0].item()) == int(rc[0]), (n, fps, preds, agg)
+    crys.crys_set_tile(crys.OP_PLAN, 0)
+
+
 def test_q1_year_invariant_on_gpu(crys, orc):
     host = datagen.q1_tables(77, 1 << 20)
     fact = {k: _dev(v) for k, v in host["fact"].items()}
