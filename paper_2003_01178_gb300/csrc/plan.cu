@@ -681,10 +681,10 @@ __global__ void __launch_bounds__(THREADS) plan_kernel(const __grid_constant__ P
     }
   };
   if constexpr (PRELOAD && ITEMS == 4) {
-    // Few tiles per block: a software pipeline.  The next tile's leading column vectors
-    // are loaded into registers before this tile is evaluated, so that their latency
-    // overlaps the evaluation instead of every warp of the SM waiting on its loads and
-    // then computing in step with the others.
+    // A software pipeline: the next tile's leading column vectors are loaded into
+    // registers before this tile is evaluated, so that their latency overlaps the
+    // evaluation instead of every warp of the SM waiting on its loads and then computing
+    // in step with the others.
     // Full tiles (all but possibly the last) load without per-group bounds tests.
     auto full_cols = [&](const GlobalCols& c) { return FullTileCols{c.cols, c.row0, c.pol}; };
     auto load = [&](int64_t tt, TileVectors<ITEMS>& r) {
@@ -774,8 +774,17 @@ __global__ void __launch_bounds__(THREADS) plan_kernel(const __grid_constant__ P
 // a direct dimension table with its field predicates, one output group, SUM(a * b) or
 // SUM(a)) compiled for their shape: no loops over plan fields, no switch on the aggregate,
 // full tiles without bounds tests, and the next tile's column vectors in flight while the
-// current one is evaluated.  Used where a block takes few tiles (the launch is short and
-// per-tile overhead shows); other plans, and long launches, take plan_kernel.
+// current one is evaluated.
+//
+// Selective loads (Section 3.3's BlockLoadSel): every warp counts the 128-byte lines of the
+// aggregate-only ("late") columns that its live rows needed (an L2 miss fills a whole
+// line, so a line is saved only when all of its 32 rows failed).  Once fewer than a third
+// were needed, the warp stops loading those columns ahead and reads them after the
+// predicates and the probe, for the 16-byte groups with a live row only; thread 0 stops
+// prefetching them into L2 (by warp 0's counts), so their dead lines stay in DRAM.  Only
+// the 4-row shapes carry this: with 8-row items its registers cost the dense case 5% (Q1
+// at 2^28 rows), so the tile-shape tuner picks between a selective 4-row and a plain 8-row
+// kernel per workload.
 template <int THREADS, int ITEMS, int NP, int AGG>
 __global__ void __launch_bounds__(THREADS) plan_fixed_kernel(const __grid_constant__ PlanArgs a) {
   static_assert(ITEMS == 4 || ITEMS == 8, "one or two 16-byte vectors per column and thread");
@@ -797,8 +806,13 @@ __global__ void __launch_bounds__(THREADS) plan_fixed_kernel(const __grid_consta
   const int32_t* kcol = a.cols[J.fk_col] + a.row_begin;
   const int32_t* xcol = a.cols[q.agg_a] + a.row_begin;
   const int32_t* ycol = a.cols[TWO ? q.agg_b : q.agg_a] + a.row_begin;
+  constexpr bool SELECTIVE = ITEMS == 4;
+  const uint32_t late_mask = SELECTIVE ? a.late_mask : 0u;
+  const bool x_late = (late_mask >> q.agg_a) & 1u;
+  const bool y_late = TWO && ((late_mask >> q.agg_b) & 1u);
   struct Vecs {
     int4 p[NP][VEC], k[VEC], x[VEC], y[VEC];
+    bool sel;  // the late columns were not loaded ahead
   };
   auto load4 = [&](const int32_t* col, int64_t row0, int p, int valid) -> int4 {
     if (p + 4 <= valid) return ld_stream_v4(col + row0 + p, pol);
@@ -807,28 +821,33 @@ __global__ void __launch_bounds__(THREADS) plan_fixed_kernel(const __grid_consta
     for (int e = 0; e < 4; ++e) v[e] = p + e < valid ? ld_stream(col + row0 + p + e, pol) : 0;
     return make_int4(v[0], v[1], v[2], v[3]);
   };
-  auto load = [&](int64_t t, Vecs& V) {
+  auto load = [&](int64_t t, Vecs& V, bool sparse) {
     const int64_t row0 = t * TILE;
     const int valid = static_cast<int>((nrows - row0) < TILE ? (nrows - row0) : TILE);
+    V.sel = sparse;
+    const bool lx = !(sparse && x_late), ly = TWO && !(sparse && y_late);
 #pragma unroll
     for (int j = 0; j < VEC; ++j) {
       const int p = (j * THREADS + tid) * 4;
+      V.x[j] = make_int4(0, 0, 0, 0);
+      V.y[j] = make_int4(0, 0, 0, 0);
       if (valid == TILE) {
 #pragma unroll
         for (int f = 0; f < NP; ++f) V.p[f][j] = ld_stream_v4(pcol[f] + row0 + p, pol);
         V.k[j] = ld_stream_v4(kcol + row0 + p, pol);
-        V.x[j] = ld_stream_v4(xcol + row0 + p, pol);
-        if (TWO) V.y[j] = ld_stream_v4(ycol + row0 + p, pol);
+        if (lx) V.x[j] = ld_stream_v4(xcol + row0 + p, pol);
+        if (ly) V.y[j] = ld_stream_v4(ycol + row0 + p, pol);
       } else {
 #pragma unroll
         for (int f = 0; f < NP; ++f) V.p[f][j] = load4(pcol[f], row0, p, valid);
         V.k[j] = load4(kcol, row0, p, valid);
-        V.x[j] = load4(xcol, row0, p, valid);
-        if (TWO) V.y[j] = load4(ycol, row0, p, valid);
+        if (lx) V.x[j] = load4(xcol, row0, p, valid);
+        if (ly) V.y[j] = load4(ycol, row0, p, valid);
       }
     }
   };
   uint64_t my_sum = 0, my_count = 0;
+  uint32_t need_lines = 0, seen_lines = 0;
   if (threadIdx.x == 0)
     for (int d = 0; d < kPrefetchTiles; ++d) {
       const int64_t tt = blockIdx.x + static_cast<int64_t>(d) * gridDim.x;
@@ -836,23 +855,23 @@ __global__ void __launch_bounds__(THREADS) plan_fixed_kernel(const __grid_consta
     }
   Vecs cur, nxt;
   int64_t t = blockIdx.x;
-  if (t < ntiles && !q.never) load(t, cur);
+  if (t < ntiles && !q.never) load(t, cur, false);
   for (; t < ntiles && !q.never; t += gridDim.x) {
+    const bool sparse = late_mask && seen_lines >= 64u && 3u * need_lines < seen_lines;
     const int64_t ahead = t + static_cast<int64_t>(kPrefetchTiles) * gridDim.x;
-    if (threadIdx.x == 0 && ahead < ntiles) prefetch_tile(a.cols, a.col_mask, a.row_begin, ahead, TILE, nrows);
+    if (threadIdx.x == 0 && ahead < ntiles)
+      prefetch_tile(a.cols, sparse ? (a.col_mask & ~late_mask) : a.col_mask, a.row_begin, ahead, TILE, nrows);
     const int64_t tn = t + gridDim.x;
-    if (tn < ntiles) load(tn, nxt);
+    if (tn < ntiles) load(tn, nxt, sparse);
     const int64_t row0 = t * TILE;
     const int valid = static_cast<int>((nrows - row0) < TILE ? (nrows - row0) : TILE);
 #pragma unroll
     for (int j = 0; j < VEC; ++j) {
       const int p = (j * THREADS + tid) * 4;
-      int32_t pv[NP][4], key[4], xv[4], yv[4];
+      int32_t pv[NP][4], key[4];
 #pragma unroll
       for (int f = 0; f < NP; ++f) unpack4(cur.p[f][j], pv[f]);
       unpack4(cur.k[j], key);
-      unpack4(cur.x[j], xv);
-      if (TWO) unpack4(cur.y[j], yv);
       // BlockPred, then the probe of the surviving rows, all four slot reads in flight
       bool ok[4];
       uint64_t slot[4];
@@ -864,19 +883,39 @@ __global__ void __launch_bounds__(THREADS) plan_fixed_kernel(const __grid_consta
         slot[e] = ok[e] && static_cast<uint32_t>(key[e]) < J.hash.limit ? ld_slot(J.slots + key[e], pol_table)
                                                                         : kEmptySlot;
       }
+      bool hit[4];
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
-        bool hit = ok[e] && slot[e] != kEmptySlot && static_cast<uint32_t>(slot[e]) == static_cast<uint32_t>(key[e]);
+        hit[e] = ok[e] && slot[e] != kEmptySlot && static_cast<uint32_t>(slot[e]) == static_cast<uint32_t>(key[e]);
         const int32_t v = static_cast<int32_t>(slot[e] >> 32);
         for (int f = 0; f < J.n_fp; ++f)
-          hit = hit && in_span(field_of(v, J.fp_shift[f], J.fp_mask[f]), J.fp_lo[f], J.fp_span[f]);
+          hit[e] = hit[e] && in_span(field_of(v, J.fp_shift[f], J.fp_mask[f]), J.fp_lo[f], J.fp_span[f]);
+      }
+      const bool live = hit[0] || hit[1] || hit[2] || hit[3];
+      if constexpr (SELECTIVE) {
+        // lanes 8m .. 8m+7 hold the 16-byte groups of 128-byte line m of the warp's 512 bytes
+        const uint32_t b = __ballot_sync(0xFFFFFFFFu, live);
+        need_lines += static_cast<uint32_t>((b & 0xFFu) != 0) + ((b & 0xFF00u) != 0) + ((b & 0xFF0000u) != 0) +
+                      ((b & 0xFF000000u) != 0);
+        seen_lines += 4u;
+      }
+      int4 x4 = cur.x[j], y4 = TWO ? cur.y[j] : make_int4(0, 0, 0, 0);
+      if (SELECTIVE && cur.sel && live) {  // the late columns of this group, read only now that a row is live
+        if (x_late) x4 = load4(xcol, row0, p, valid);
+        if (y_late) y4 = load4(ycol, row0, p, valid);
+      }
+      int32_t xv[4], yv[4];
+      unpack4(x4, xv);
+      unpack4(y4, yv);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
         int64_t r;
         if (AGG == CRYS_AGG_A_MUL_B) r = static_cast<int64_t>(xv[e]) * yv[e];
         else if (AGG == CRYS_AGG_A_SUB_B) r = static_cast<int64_t>(xv[e]) - yv[e];
         else if (AGG == CRYS_AGG_A_ADD_B) r = static_cast<int64_t>(xv[e]) + yv[e];
         else r = xv[e];
-        my_sum += hit ? static_cast<uint64_t>(r) : 0ull;
-        my_count += hit ? 1u : 0u;
+        my_sum += hit[e] ? static_cast<uint64_t>(r) : 0ull;
+        my_count += hit[e] ? 1u : 0u;
       }
     }
     cur = nxt;
@@ -1627,20 +1666,22 @@ int launch_plan(PlanArgs& a, cudaStream_t s) {
   } else {
     a.q.acc_mode = kAccGlobal;
   }
-  // With few tiles per block the kernel waits on each tile's loads in turn: then all of
-  // a tile's loads go out together (4- and 8-row items); with many tiles per block the
-  // lighter looping evaluation keeps more blocks resident.
+  // All of a tile's leading column loads go out together (4- and 8-row items), and with
+  // 4-row items the next tile's loads are in flight while a tile is evaluated: measured
+  // faster than the step-by-step evaluation at every size (Q1 at 2^28 rows, hashed date
+  // table: 0.665 against 0.818 ms).  The step-by-step evaluation, with selective loads of
+  // the late columns, remains for other tile shapes.
   const int64_t ntiles = (a.row_end - a.row_begin + TILE - 1) / TILE;
   auto kl = plan_kernel<THREADS, ITEMS, false>;
   if (!allow_smem(kl, smem)) return CRYS_ECUDA;
   int grid = persistent_grid(kl, THREADS, smem, ntiles);
-  const bool preload = (ITEMS == 4 || ITEMS == 8) && ntiles <= 8 * static_cast<int64_t>(grid);
+  const bool preload = ITEMS == 4 || ITEMS == 8;
   auto k = preload ? plan_kernel<THREADS, ITEMS, true> : kl;
   if (preload) {
     if (!allow_smem(k, smem)) return CRYS_ECUDA;
     grid = persistent_grid(k, THREADS, smem, ntiles);
   }
-  // a plan of the Q1 family in a short launch: the kernel compiled for its shape
+  // a plan of the Q1 family: the kernel compiled for its shape
   const DevJoin& J0 = a.q.joins[0];
   const bool fixed = preload && a.q.acc_mode == kAccSingle && a.q.n_joins == 1 &&
                      (a.q.n_preds == 1 || a.q.n_preds == 2) && J0.card <= 0 && J0.hash.steps == 0u &&
