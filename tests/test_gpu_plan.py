@@ -100,6 +100,58 @@ def test_fixed_shape_plans(crys, orc, n, variant):
     crys.crys_set_tile(crys.OP_PLAN, 0)
 
 
+@pytest.mark.parametrize("variant", [2, 3])
+def test_fixed_shape_selective_loads(crys, orc, variant):
+    """Long launches with 4-row tiles: once a warp has seen that fewer than a third of the
+    aggregate-only column's 128-byte lines are needed, it reads that column for live
+    16-byte groups only; sums stay exact for sparse and dense plans alike."""
+    crys.crys_set_tile(crys.OP_PLAN, variant)
+    n = (1 << 25) + 3
+    host = datagen.q1_tables(123, n)
+    fact = {k: _dev(v) for k, v in host["fact"].items()}
+    dim = {k: _dev(v) for k, v in host["dim"].items()}
+    ht = crys.HashTable.build(dim["key"], dim["yr"], filters=[(dim["yr"], 3, 3)], capacity=dim["key"].numel(),
+                              kind=crys.HASH_DIRECT)
+    cols = [fact["fk"], fact["a"], fact["b"], fact["c"]]
+    hcols = [host["fact"][k] for k in ("fk", "a", "b", "c")]
+    ojoin = [{"fk_col": 0, "keys": host["dim"]["key"], "preds": [(host["dim"]["yr"], 3, 3)], "group": None,
+              "card": 1}]
+    for preds, agg in [([(1, 1, 1), (2, 1, 3)], ("mul", 3, 2)),   # 0.08% of rows: late column c read sparsely
+                       ([(1, 1, 1)], ("mul", 3, 2)),               # two late columns (b, c)
+                       ([(1, I32_MIN, 24), (2, 1, 3)], ("mul", 3, 2))]:  # the stated query (dense)
+        sums, counts = crys.run_plan(cols, preds, [(0, ht, 0)], agg)
+        rs, rc = orc.run_plan_raw(hcols, preds, ojoin, agg)
+        assert int(sums[0].item()) == int(rs[0]) and int(counts[0].item()) == int(rc[0]), (preds, agg)
+    crys.crys_set_tile(crys.OP_PLAN, 0)
+
+
+def test_run_plan_in_cuda_graph(crys, orc):
+    """A captured call (the output-clearing kernel, then the query kernel launched as its
+    programmatic dependent) replays exactly, again and again."""
+    n = 1_000_003
+    host = datagen.q1_tables(7, n)
+    fact = {k: _dev(v) for k, v in host["fact"].items()}
+    dim = {k: _dev(v) for k, v in host["dim"].items()}
+    ht = crys.HashTable.build(dim["key"], dim["yr"], filters=[(dim["yr"], 3, 3)], capacity=dim["key"].numel(),
+                              kind=crys.HASH_DIRECT)
+    table = crys.make_table([fact["fk"], fact["a"], fact["b"], fact["c"]])
+    sums = torch.zeros(1, dtype=torch.int64, device="cuda")
+    counts = torch.zeros(1, dtype=torch.int64, device="cuda")
+    plan = crys.make_plan([(1, I32_MIN, 24), (2, 1, 3)], [(0, ht, 0)], ("mul", 3, 2), sums, counts)
+    expect = orc.q1_run(host["fact"], host["dim"])
+    crys.crys_run_plan(table, plan)  # attributes and caches outside the capture
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        crys.crys_run_plan(table, plan, torch.cuda.current_stream())
+    for _ in range(3):
+        sums.fill_(-1)
+        counts.fill_(-1)
+        g.replay()
+        torch.cuda.synchronize()
+        assert int(sums.item()) == expect
+
+
 def test_q1_year_invariant_on_gpu(crys, orc):
     host = datagen.q1_tables(77, 1 << 20)
     fact = {k: _dev(v) for k, v in host["fact"].items()}
