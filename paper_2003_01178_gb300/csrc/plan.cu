@@ -1651,6 +1651,16 @@ int zero_outputs(const DevQuery& q, cudaStream_t s) {
   return CRYS_OK;
 }
 
+// Clears a query's outputs on the stream: the kernel the query kernel is launched behind
+// (programmatic dependent launch).
+int launch_zero_outputs(const DevQuery& q, cudaStream_t s) {
+  const int64_t zb = q.groups > 256 ? (q.groups + 255) / 256 : 1;
+  const int64_t zcap = static_cast<int64_t>(sm_count()) * 4;
+  zero_outputs_kernel<<<static_cast<unsigned>(zb < zcap ? zb : zcap), 256, 0, s>>>(q.sums, q.counts, q.groups);
+  note_launch();
+  return check_launch();
+}
+
 // Per-block accumulators are 32-bit counts: a block must see fewer than 2^32 rows.
 bool counts_fit(int64_t rows, int grid) { return (rows / (grid > 0 ? grid : 1)) + (1 << 16) < (1ll << 32); }
 
@@ -1696,7 +1706,9 @@ int launch_plan(PlanArgs& a, cudaStream_t s) {
     grid = persistent_grid(k, THREADS, 0, ntiles);
   }
   if (!counts_fit(a.row_end - a.row_begin, grid)) return CRYS_EINVAL;
-  // launched while zero_outputs_kernel (issued just before on this stream) still runs
+  // every host check passed: clear the outputs, then launch the query kernel while the
+  // clearing kernel still runs
+  if (launch_zero_outputs(a.q, s) != CRYS_OK) return CRYS_ECUDA;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(static_cast<unsigned>(grid));
   cfg.blockDim = dim3(THREADS);
@@ -2128,15 +2140,7 @@ int crys_run_plan(const crys_table* fact, const crys_plan* plan, crys_stream str
   a.err = device_error_word();
   if (!a.err) return CRYS_ECUDA;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  {
-    const int64_t zb = a.q.groups > 256 ? (a.q.groups + 255) / 256 : 1;
-    const int64_t zcap = static_cast<int64_t>(sm_count()) * 4;
-    zero_outputs_kernel<<<static_cast<unsigned>(zb < zcap ? zb : zcap), 256, 0, s>>>(a.q.sums, a.q.counts,
-                                                                                      a.q.groups);
-    note_launch();
-    if (check_launch() != CRYS_OK) return CRYS_ECUDA;
-  }
-  if (fact->n_rows == 0) return CRYS_OK;
+  if (fact->n_rows == 0) return launch_zero_outputs(a.q, s) == CRYS_OK ? CRYS_OK : CRYS_ECUDA;
   constexpr int kOp = CRYS_OP_PLAN;
   switch (tile_variant(kOp)) {
     case 1: return launch_plan<kTiles[kOp][1].threads, kTiles[kOp][1].items>(a, s);
