@@ -232,6 +232,51 @@ __device__ __forceinline__ bool hash_resolve(const uint64_t* slots, const HashFn
   }
 }
 
+// Continues ITEMS lookups whose home slots were already loaded, all together (Section 4.3,
+// linear probing): every round issues the next slot of each unresolved item before any
+// of them is examined, so a warp waits one L2 round trip per probing step of its
+// longest chain instead of one per item whose chain goes past the home slot.  Items
+// outside `live` are never found.  Returns the bitmap of items whose key was found, with
+// its value in `value`; `h` and `s` are consumed.
+template <int ITEMS>
+__device__ __forceinline__ uint32_t hash_resolve_all(const uint64_t* slots, const HashFn& f,
+                                                     uint32_t (&h)[ITEMS], uint64_t (&s)[ITEMS],
+                                                     const int32_t (&key)[ITEMS], uint32_t live,
+                                                     int32_t (&value)[ITEMS], uint64_t pol) {
+  uint32_t found = 0, pend = 0;
+#pragma unroll
+  for (int i = 0; i < ITEMS; ++i) {
+    const uint32_t bit = ((live >> i) & 1u) << i;
+    if (s[i] == kEmptySlot || !bit) continue;
+    if (static_cast<uint32_t>(s[i]) == static_cast<uint32_t>(key[i])) {
+      value[i] = static_cast<int32_t>(s[i] >> 32);
+      found |= bit;
+    } else {
+      pend |= bit;
+    }
+  }
+  for (uint32_t probe = 0; pend != 0u && probe < f.steps; ++probe) {
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i)
+      if ((pend >> i) & 1u) {
+        h[i] = (h[i] + 1) & f.mask;
+        s[i] = ld_slot(slots + h[i], pol);
+      }
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i)
+      if ((pend >> i) & 1u) {
+        if (s[i] == kEmptySlot) {
+          pend &= ~(1u << i);
+        } else if (static_cast<uint32_t>(s[i]) == static_cast<uint32_t>(key[i])) {
+          value[i] = static_cast<int32_t>(s[i] >> 32);
+          found |= 1u << i;
+          pend &= ~(1u << i);
+        }
+      }
+  }
+  return found;
+}
+
 // Looks `key` up; returns the value, or false when absent.
 __device__ __forceinline__ bool hash_find(const uint64_t* slots, const HashFn& f, int32_t key,
                                           int32_t* value, uint64_t pol) {

@@ -3,7 +3,8 @@
 //
 // Probe kernel per tile: BlockLoad of the key and payload tiles (bulk copies into a
 // shared-memory stage), BlockLookup with the first slot of every item loaded before any
-// is resolved (ITEMS independent random reads in flight per thread), per-thread int64
+// is resolved (ITEMS independent random reads in flight per thread), continuations past
+// the home slots issued a probing step at a time for all items together, per-thread int64
 // sums, and BlockAggregate once per persistent block (one atomic per block).  A table of
 // at most 32 KB is first copied into each block's shared memory and probed there.
 #include "common.cuh"
@@ -191,15 +192,25 @@ __global__ void __launch_bounds__(THREADS) probe_kernel(ProbeArgs a) {
       else
         slot[i] = look ? ld_slot(a.slots + h[i], pol_table) : kEmptySlot;
     }
+    if (SMEM_TABLE) {
 #pragma unroll
-    for (int i = 0; i < ITEMS; ++i) {
-      int32_t value;
-      const bool hit = SMEM_TABLE ? resolve_smem(h[i], slot[i], key[i], &value)
-                                  : hash_resolve(a.slots, a.hash, h[i], slot[i], key[i], &value, pol_table);
-      if (((live >> i) & 1u) && hit) {
-        sum += static_cast<uint64_t>(static_cast<int64_t>(pay[i]) * static_cast<int64_t>(value));
-        matches += 1;
+      for (int i = 0; i < ITEMS; ++i) {
+        int32_t value;
+        if (((live >> i) & 1u) && resolve_smem(h[i], slot[i], key[i], &value)) {
+          sum += static_cast<uint64_t>(static_cast<int64_t>(pay[i]) * static_cast<int64_t>(value));
+          matches += 1;
+        }
       }
+    } else {
+      // continuations past the home slot: one round trip per probing step for all items
+      int32_t value[ITEMS];
+      const uint32_t found = hash_resolve_all<ITEMS>(a.slots, a.hash, h, slot, key, live, value, pol_table);
+#pragma unroll
+      for (int i = 0; i < ITEMS; ++i)
+        if ((found >> i) & 1u) {
+          sum += static_cast<uint64_t>(static_cast<int64_t>(pay[i]) * static_cast<int64_t>(value[i]));
+          matches += 1;
+        }
     }
     __syncthreads();
     if (tid == 0) {

@@ -134,7 +134,7 @@ __device__ __forceinline__ void unpack4(int4 q, int32_t* dst) {
 }
 
 // Probes one table for this thread's ITEMS rows: all first-slot reads are issued before
-// any is resolved.  Returns the bitmap of rows whose key was found; values in `value`.
+// any is resolved, and continuations a probing step at a time for all rows together.  Returns the bitmap of rows whose key was found; values in `value`.
 template <int ITEMS>
 __device__ __forceinline__ uint32_t probe_items(const uint64_t* slots, const HashFn& hf,
                                                 const int32_t (&key)[ITEMS], uint32_t live,
@@ -161,14 +161,9 @@ __device__ __forceinline__ uint32_t probe_items(const uint64_t* slots, const Has
     h[i] = hash_slot(key[i], hf);
     slot[i] = ((live >> i) & 1u) && hash_may_hold(key[i], hf) ? ld_slot(slots + h[i], pol) : kEmptySlot;
   }
-  uint32_t found = 0;
 #pragma unroll
-  for (int i = 0; i < ITEMS; ++i) {
-    value[i] = 0;
-    if (((live >> i) & 1u) && hash_resolve(slots, hf, h[i], slot[i], key[i], &value[i], pol))
-      found |= 1u << i;
-  }
-  return found;
+  for (int i = 0; i < ITEMS; ++i) value[i] = 0;
+  return hash_resolve_all<ITEMS>(slots, hf, h, slot, key, live, value, pol);
 }
 
 // Range test lo <= v <= hi as one unsigned comparison (span = hi - lo).
@@ -1026,14 +1021,10 @@ __global__ void __launch_bounds__(THREADS, (24 * kWarp) / THREADS > 0 ? (24 * kW
         if (d >= a.n_probes) break;
         const ProbeSpec& P = a.probes[d];
         int32_t value[ITEMS];
-        uint32_t found = 0;
 #pragma unroll
-        for (int i = 0; i < ITEMS; ++i) {
-          value[i] = 0;
-          if (((live >> i) & 1u) &&
-              hash_resolve(P.slots, P.hash, h[dd][i], slot[dd][i], key[dd][i], &value[i], pol_table))
-            found |= 1u << i;
-        }
+        for (int i = 0; i < ITEMS; ++i) value[i] = 0;
+        const uint32_t found =
+            hash_resolve_all<ITEMS>(P.slots, P.hash, h[dd], slot[dd], key[dd], live, value, pol_table);
         pf[d * THREADS + tid] = found;
 #pragma unroll
         for (int j = 0; j < VEC; ++j)
@@ -1111,8 +1102,10 @@ __global__ void __launch_bounds__(THREADS, (24 * kWarp) / THREADS > 0 ? (24 * kW
 constexpr int kMaxTagPairs = 8;
 // Tagged-scan blocks resident per SM: two blocks of 512 threads (32 warps) measured
 // faster than three of 256, with the same shared memory left to each block's group
-// accumulators.
-constexpr int kTagBlocksPerSM = 2;
+// accumulators.  A block of 1024 threads has the SM to itself: its shared memory also
+// holds the entries of the batch's smallest table (see kTagSmemBytes), which two blocks
+// could only hold twice.
+__host__ __device__ constexpr int tag_blocks_per_sm(int threads) { return threads >= 1024 ? 1 : 2; }
 constexpr int kMaxTagEntries = CRYS_MAX_PLANS * CRYS_MAX_JOINS;
 // A query's descriptor: kDescWords 32-bit fields (a column field holds the index of the
 // column's value region), stored field-major in shared memory: field f of query q at
@@ -1202,6 +1195,10 @@ struct TagScanPair {
 // Entries of a table up to this size are read through L1, where every tile's lookups
 // find them; the others bypass L1 so that they do not evict the small ones.
 constexpr int64_t kTagL1Bytes = 24 * 1024;
+// In a block that has its SM to itself, the entries of one table up to this size are
+// copied into shared memory once and looked up there: a warp's 32 random lookups then
+// cost a few bank-conflict wavefronts instead of one L1 request per distinct line.
+constexpr int64_t kTagSmemBytes = 24 * 1024;
 
 __device__ __forceinline__ uint64_t ld_tag_l1(const uint64_t* p, uint64_t pol) {
   uint64_t v;
@@ -1231,6 +1228,8 @@ struct TagHead {
   TagScanPair pairs[kMaxTagPairs];
   int32_t n_stage;                    // fact columns staged for finishing
   int32_t stage_col[CRYS_MAX_COLS];   // staged column s -> fact column (region n_pairs + s)
+  int32_t smem_pair;                  // pair whose entries are looked up in shared memory, or -1
+  int32_t smem_slots;                 // its entries (its table's capacity)
 };
 
 struct TagArgs : TagHead {
@@ -1293,7 +1292,8 @@ __device__ __forceinline__ void finish_pair(const DescView<const int32_t> D, con
 }
 
 // Shared memory of a block: query descriptors, the value regions of the tile's rows
-// (n_vals = pairs + staged columns, PVS words each), one (row, query) list per warp, then
+// (n_vals = pairs + staged columns, PVS words each), one (row, query) list per warp, the
+// entries of the pair looked up in shared memory (tag_slots of them, possibly none), then
 // the group accumulators.
 template <int THREADS, int ITEMS>
 struct TagSmem {
@@ -1303,7 +1303,12 @@ struct TagSmem {
   static constexpr size_t desc_bytes = CRYS_MAX_PLANS * kDescWords * 4;
   static constexpr size_t vals_off = (desc_bytes + 15) / 16 * 16;
   __host__ __device__ static size_t list_off(int n_vals) { return vals_off + static_cast<size_t>(n_vals) * PVS * 4; }
-  __host__ __device__ static size_t acc_off(int n_vals) { return list_off(n_vals) + static_cast<size_t>(THREADS / kWarp) * LIST * 2; }
+  __host__ __device__ static size_t tags_off(int n_vals) {
+    return (list_off(n_vals) + static_cast<size_t>(THREADS / kWarp) * LIST * 2 + 15) / 16 * 16;
+  }
+  __host__ __device__ static size_t acc_off(int n_vals, int tag_slots) {
+    return tags_off(n_vals) + static_cast<size_t>(tag_slots) * 8;
+  }
 };
 
 template <int THREADS, int ITEMS>
@@ -1311,7 +1316,7 @@ __device__ __forceinline__ void tagged_scan_body(const TagHead& a, const int32_t
   using L = TagSmem<THREADS, ITEMS>;
   constexpr int TILE = L::TILE;
   constexpr int VEC = ITEMS / 4;
-  static_assert(TILE <= 2048, "a list entry holds an 11-bit tile row");
+  static_assert(ITEMS <= 8, "a list entry holds a 3-bit item slot and a lane");
   constexpr int PVS = L::PVS;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int tid = threadIdx.x, lane = tid % kWarp, warp = tid / kWarp;
@@ -1319,17 +1324,25 @@ __device__ __forceinline__ void tagged_scan_body(const TagHead& a, const int32_t
   int32_t* desc = reinterpret_cast<int32_t*>(smem_raw);
   int32_t* vals = reinterpret_cast<int32_t*>(smem_raw + L::vals_off);
   uint16_t* list = reinterpret_cast<uint16_t*>(smem_raw + L::list_off(n_vals)) + warp * L::LIST;
+  uint64_t* stag = reinterpret_cast<uint64_t*>(smem_raw + L::tags_off(n_vals));
+  const int tag_slots = a.smem_pair >= 0 ? a.smem_slots : 0;
   // arguments prepared for another tile shape, or accumulators past the shared memory
   // this launch has: refuse the work (uniformly in every block) instead of overrunning
   uint32_t dyn_smem;
   asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn_smem));
   if (a.tile_shape != ((THREADS << 16) | ITEMS) || a.n_stage < 1 || a.n_stage > CRYS_MAX_COLS ||
-      L::acc_off(n_vals) + static_cast<size_t>(a.shared_groups) * 12 > dyn_smem) {
+      a.smem_pair >= a.n_pairs || tag_slots < 0 ||
+      (a.smem_pair >= 0 && static_cast<uint32_t>(tag_slots) != a.pairs[a.smem_pair].limit) ||
+      L::acc_off(n_vals, tag_slots) + static_cast<size_t>(a.shared_groups) * 12 > dyn_smem) {
     if (tid == 0) set_error(a.err, CRYS_DEV_BOUNDS);
     return;
   }
-  const SharedAcc acc = shared_acc(smem_raw + L::acc_off(n_vals), a.shared_groups);
+  const SharedAcc acc = shared_acc(smem_raw + L::acc_off(n_vals, tag_slots), a.shared_groups);
   for (int w = tid; w < CRYS_MAX_PLANS * kDescWords; w += THREADS) desc[w] = desc_src[w];
+  if (a.smem_pair >= 0) {
+    const uint64_t* src = a.pairs[a.smem_pair].ann;
+    for (int w = tid; w < tag_slots; w += THREADS) stag[w] = src[w];
+  }
   for (int g = tid; g < a.shared_groups; g += THREADS) {
     acc.sums[g] = 0;
     acc.counts[g] = 0;
@@ -1367,7 +1380,11 @@ __device__ __forceinline__ void tagged_scan_body(const TagHead& a, const int32_t
 #pragma unroll
       for (int j = 0; j < VEC; ++j) unpack4(fk_cols.load4(P.fk_col, (j * THREADS + tid) * 4), key + 4 * j);
       uint64_t e[ITEMS];
-      if (P.in_l1) {
+      if (p == a.smem_pair) {
+#pragma unroll
+        for (int i = 0; i < ITEMS; ++i)
+          e[i] = (rm[i] && static_cast<uint32_t>(key[i]) < P.limit) ? stag[key[i]] : static_cast<uint64_t>(P.nonjoin);
+      } else if (P.in_l1) {
 #pragma unroll
         for (int i = 0; i < ITEMS; ++i)
           e[i] = (rm[i] && static_cast<uint32_t>(key[i]) < P.limit) ? ld_tag_l1(P.ann + key[i], pol_table)
@@ -1408,25 +1425,26 @@ __device__ __forceinline__ void tagged_scan_body(const TagHead& a, const int32_t
       const int total_s = __shfl_sync(0xFFFFFFFFu, incl_s, kWarp - 1);
       const int total = total_s + __shfl_sync(0xFFFFFFFFu, incl_g, kWarp - 1);
       if (total == 0) continue;
-      const int r = i * THREADS + tid;  // item-major index of the lane's row
+      const int r = (i << 5) | lane;  // the lane's row within the warp's rows
       // the pairs go through the list in windows of L::LIST entries (one window unless
       // the round expands more pairs than that)
       for (int w0 = 0; w0 < total; w0 += L::LIST) {
         int k = incl_s - ns;
         for (uint32_t m = ms; m; m &= m - 1, ++k)
           if (k >= w0 && k < w0 + L::LIST)
-            list[k - w0] = static_cast<uint16_t>(((__ffs(m) - 1) << 11) | r);
+            list[k - w0] = static_cast<uint16_t>(((__ffs(m) - 1) << 8) | r);
         k = total_s + incl_g - ng;
         for (uint32_t m = mg; m; m &= m - 1, ++k)
           if (k >= w0 && k < w0 + L::LIST)
-            list[k - w0] = static_cast<uint16_t>(((__ffs(m) - 1) << 11) | r);
+            list[k - w0] = static_cast<uint16_t>(((__ffs(m) - 1) << 8) | r);
         __syncwarp();
         const int wn = (total - w0) < L::LIST ? (total - w0) : L::LIST;
         for (int base = 0; base < wn; base += kWarp) {
           if (base + lane < wn) {
             const uint32_t ent = list[base + lane];
-            finish_pair<PVS>(DescView<const int32_t>{desc + (ent >> 11)}, vals, static_cast<int>(ent & 0x7FFu), acc,
-                             a.err);
+            // item-major index of the entry's row: item slot, then the warp's lane
+            const int row = static_cast<int>((ent >> 5) & 7u) * THREADS + warp * kWarp + static_cast<int>(ent & 31u);
+            finish_pair<PVS>(DescView<const int32_t>{desc + (ent >> 8)}, vals, row, acc, a.err);
           }
         }
         __syncwarp();  // the list is reused by the next window or item slot
@@ -1448,7 +1466,7 @@ __device__ __forceinline__ void tagged_scan_body(const TagHead& a, const int32_t
 }
 
 template <int THREADS, int ITEMS>
-__global__ void __launch_bounds__(THREADS, kTagBlocksPerSM)
+__global__ void __launch_bounds__(THREADS, tag_blocks_per_sm(THREADS))
     tagged_scan_kernel(const __grid_constant__ TagArgs a) {
   // the head is read on every tile: a shared-memory copy is cheaper than the parameter
   // bank, whose cache does not hold a 9 KB argument block
@@ -1494,7 +1512,7 @@ __global__ void __launch_bounds__(256) prepare_kernel(const TagLaunch* __restric
 }
 
 template <int THREADS, int ITEMS>
-__global__ void __launch_bounds__(THREADS, kTagBlocksPerSM)
+__global__ void __launch_bounds__(THREADS, tag_blocks_per_sm(THREADS))
     tagged_scan_kernel_dev(const TagArgs* __restrict__ a) {
   // the head is read on every tile: one shared-memory copy per block
   __shared__ __align__(16) TagHead head;
@@ -1895,6 +1913,8 @@ bool tag_batch(const crys_plan* plans, const DevQuery* q, int n, TagBatch* tb) {
     S.stage_col[c] = 0;
   }
   S.n_stage = 0;
+  S.smem_pair = -1;
+  S.smem_slots = 0;
   auto region = [&](int32_t c) {
     if (region_of[c] < 0) {
       region_of[c] = A.n_pairs + S.n_stage;
@@ -2003,15 +2023,35 @@ int64_t assign_accumulators(TagArgs& S, const DevQuery* q, size_t budget) {
   return used;
 }
 
-constexpr size_t kTagShare = (220u * 1024u) / kTagBlocksPerSM;  // shared memory of one block
+// Shared memory of one tagged-scan block.
+constexpr size_t tag_share(int threads) { return (220u * 1024u) / tag_blocks_per_sm(threads); }
+
+// The pair whose entries a block of this shape looks up in shared memory: the smallest
+// table of at most kTagSmemBytes, in blocks that have their SM to itself (-1: none).
+template <int THREADS>
+void choose_smem_pair(TagArgs& S) {
+  S.smem_pair = -1;
+  S.smem_slots = 0;
+  if constexpr (tag_blocks_per_sm(THREADS) == 1) {
+    for (int p = 0; p < S.n_pairs; ++p) {
+      const int64_t bytes = static_cast<int64_t>(S.pairs[p].limit) * 8;
+      if (bytes <= kTagSmemBytes && (S.smem_pair < 0 || S.pairs[p].limit < S.pairs[S.smem_pair].limit)) {
+        S.smem_pair = p;
+        S.smem_slots = static_cast<int32_t>(S.pairs[p].limit);
+      }
+    }
+  }
+}
 
 template <int THREADS, int ITEMS>
 int launch_tagged(TagBatch& tb, const DevQuery* q, unsigned char* scratch, cudaStream_t s) {
   using L = TagSmem<THREADS, ITEMS>;
   constexpr int TILE = L::TILE;
+  constexpr size_t kTagShare = tag_share(THREADS);
   AnnotateArgs& A = tb.ann;
   TagArgs& S = tb.scan;
   place_annotations(tb, scratch);
+  choose_smem_pair<THREADS>(S);
   if (A.n_pairs > 0) {
     int64_t gx = (tb.max_slots + 255) / 256;
     const int64_t cap = static_cast<int64_t>(sm_count()) * 8;
@@ -2021,7 +2061,12 @@ int launch_tagged(TagBatch& tb, const DevQuery* q, unsigned char* scratch, cudaS
     const int rc = check_launch();
     if (rc != CRYS_OK) return rc;
   }
-  const size_t fixed = L::acc_off(S.n_pairs + S.n_stage);
+  size_t fixed = L::acc_off(S.n_pairs + S.n_stage, S.smem_slots);
+  if (fixed > kTagShare && S.smem_pair >= 0) {  // no room for the entries: read them through L1
+    S.smem_pair = -1;
+    S.smem_slots = 0;
+    fixed = L::acc_off(S.n_pairs + S.n_stage, 0);
+  }
   const int64_t used = assign_accumulators(S, q, kTagShare > fixed ? kTagShare - fixed : 0);
   S.tile_shape = (THREADS << 16) | ITEMS;
   S.smem_bytes = static_cast<int32_t>(fixed + static_cast<size_t>(used) * 12);
@@ -2039,6 +2084,7 @@ int launch_tagged(TagBatch& tb, const DevQuery* q, unsigned char* scratch, cudaS
 // memory depend only on the shape, so the launch can be captured once and replayed.
 template <int THREADS, int ITEMS>
 int fixed_scan_grid(int* grid) {
+  constexpr size_t kTagShare = tag_share(THREADS);
   auto k = tagged_scan_kernel_dev<THREADS, ITEMS>;
   if (!allow_smem(k, kTagShare)) return CRYS_ECUDA;
   *grid = persistent_grid(k, THREADS, kTagShare, int64_t{1} << 40);
@@ -2048,9 +2094,16 @@ int fixed_scan_grid(int* grid) {
 template <int THREADS, int ITEMS>
 int prepare_block(TagBatch& tb, const DevQuery* q, unsigned char* scratch, TagLaunch* out) {
   using L = TagSmem<THREADS, ITEMS>;
+  constexpr size_t kTagShare = tag_share(THREADS);
   place_annotations(tb, scratch);
   TagArgs& S = tb.scan;
-  const size_t fixed = L::acc_off(S.n_pairs + S.n_stage);
+  choose_smem_pair<THREADS>(S);
+  size_t fixed = L::acc_off(S.n_pairs + S.n_stage, S.smem_slots);
+  if (fixed > kTagShare && S.smem_pair >= 0) {  // no room for the entries: read them through L1
+    S.smem_pair = -1;
+    S.smem_slots = 0;
+    fixed = L::acc_off(S.n_pairs + S.n_stage, 0);
+  }
   if (fixed > kTagShare) return CRYS_EINVAL;
   assign_accumulators(S, q, kTagShare - fixed);
   S.tile_shape = (THREADS << 16) | ITEMS;
@@ -2073,7 +2126,7 @@ int launch_block(const TagLaunch* dev, cudaStream_t s) {
   note_launch();
   rc = check_launch();
   if (rc != CRYS_OK) return rc;
-  tagged_scan_kernel_dev<THREADS, ITEMS><<<grid, THREADS, kTagShare, s>>>(&dev->scan);
+  tagged_scan_kernel_dev<THREADS, ITEMS><<<grid, THREADS, tag_share(THREADS), s>>>(&dev->scan);
   note_launch();
   return check_launch();
 }

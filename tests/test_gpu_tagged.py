@@ -188,7 +188,7 @@ def test_tagged_every_row_expands_every_query(crys, orc, world):
         assert np.array_equal(s.cpu().numpy(), rs) and np.array_equal(c.cpu().numpy(), rc)
 
 
-@pytest.mark.parametrize("variant", [0, 3])
+@pytest.mark.parametrize("variant", [0, 2, 3])
 def test_tagged_every_fact_column_finishes(crys, orc, world, variant):
     """Every fact column is read by some query's predicates or aggregate (foreign-key
     columns included), through all four (column, table) pairs, with more than two fact
