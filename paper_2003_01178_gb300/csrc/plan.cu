@@ -1414,40 +1414,62 @@ __device__ __forceinline__ void tagged_scan_body(const TagHead& a, const int32_t
       for (int i = 0; i < ITEMS; ++i) vals[(a.n_pairs + c) * PVS + i * THREADS + tid] = x[i];
     }
     __syncwarp();  // values of the warp's rows visible to all its lanes
-    // per item slot: expand each lane's (row, query) pairs into the warp's list, finish them.
-    // Pairs of queries with shared-memory accumulators come first in the list and those
-    // with global ones after, so that all but one round take a single accumulation path.
+    // Item slots SLOTS at a time: expand each lane's (row, query) pairs of those slots into
+    // the warp's list, then finish them 32 at a time (one pair per lane).  Two slots per
+    // list leave fewer partly filled rounds than one.  Pairs of queries with shared-memory
+    // accumulators come first in the list and those with global ones after, so that all
+    // but one round take a single accumulation path.
+    constexpr int SLOTS = ITEMS % 2 == 0 ? 2 : 1;
+    auto finish_window = [&](int wn) {
+      for (int base = 0; base < wn; base += kWarp) {
+        if (base + lane < wn) {
+          const uint32_t ent = list[base + lane];
+          // item-major index of the entry's row: item slot, then the warp's lane
+          const int row = static_cast<int>((ent >> 5) & 7u) * THREADS + warp * kWarp + static_cast<int>(ent & 31u);
+          finish_pair<PVS>(DescView<const int32_t>{desc + (ent >> 8)}, vals, row, acc, a.err);
+        }
+      }
+    };
 #pragma unroll
-    for (int i = 0; i < ITEMS; ++i) {
-      const uint32_t ms = rm[i] & ~a.global_mask, mg = rm[i] & a.global_mask;
-      const int ns = __popc(ms), ng = __popc(mg);
+    for (int i = 0; i < ITEMS; i += SLOTS) {
+      // bit 32 s + q: query q on the lane's row of item slot i + s
+      uint64_t ms = 0, mg = 0;
+#pragma unroll
+      for (int s = 0; s < SLOTS; ++s) {
+        ms |= static_cast<uint64_t>(rm[i + s] & ~a.global_mask) << (32 * s);
+        mg |= static_cast<uint64_t>(rm[i + s] & a.global_mask) << (32 * s);
+      }
+      const int ns = __popcll(ms), ng = __popcll(mg);
       const int incl_s = warp_inclusive_scan(ns, lane), incl_g = warp_inclusive_scan(ng, lane);
       const int total_s = __shfl_sync(0xFFFFFFFFu, incl_s, kWarp - 1);
       const int total = total_s + __shfl_sync(0xFFFFFFFFu, incl_g, kWarp - 1);
       if (total == 0) continue;
-      const int r = (i << 5) | lane;  // the lane's row within the warp's rows
-      // the pairs go through the list in windows of L::LIST entries (one window unless
-      // the round expands more pairs than that)
+      // list entry: query << 8 | item slot << 5 | lane
+      auto entry = [&](uint64_t m) {
+        const int b = __ffsll(static_cast<long long>(m)) - 1;
+        return static_cast<uint16_t>(((b & 31) << 8) | ((i + (b >> 5)) << 5) | lane);
+      };
+      if (total <= L::LIST) {  // the usual case: one window
+        int k = incl_s - ns;
+        for (uint64_t m = ms; m; m &= m - 1, ++k) list[k] = entry(m);
+        k = total_s + incl_g - ng;
+        for (uint64_t m = mg; m; m &= m - 1, ++k) list[k] = entry(m);
+        __syncwarp();
+        finish_window(total);
+        __syncwarp();  // the list is reused by the next slots
+        continue;
+      }
+      // more pairs than the list holds: windows of L::LIST entries
       for (int w0 = 0; w0 < total; w0 += L::LIST) {
         int k = incl_s - ns;
-        for (uint32_t m = ms; m; m &= m - 1, ++k)
-          if (k >= w0 && k < w0 + L::LIST)
-            list[k - w0] = static_cast<uint16_t>(((__ffs(m) - 1) << 8) | r);
+        for (uint64_t m = ms; m; m &= m - 1, ++k)
+          if (k >= w0 && k < w0 + L::LIST) list[k - w0] = entry(m);
         k = total_s + incl_g - ng;
-        for (uint32_t m = mg; m; m &= m - 1, ++k)
-          if (k >= w0 && k < w0 + L::LIST)
-            list[k - w0] = static_cast<uint16_t>(((__ffs(m) - 1) << 8) | r);
+        for (uint64_t m = mg; m; m &= m - 1, ++k)
+          if (k >= w0 && k < w0 + L::LIST) list[k - w0] = entry(m);
         __syncwarp();
-        const int wn = (total - w0) < L::LIST ? (total - w0) : L::LIST;
-        for (int base = 0; base < wn; base += kWarp) {
-          if (base + lane < wn) {
-            const uint32_t ent = list[base + lane];
-            // item-major index of the entry's row: item slot, then the warp's lane
-            const int row = static_cast<int>((ent >> 5) & 7u) * THREADS + warp * kWarp + static_cast<int>(ent & 31u);
-            finish_pair<PVS>(DescView<const int32_t>{desc + (ent >> 8)}, vals, row, acc, a.err);
-          }
-        }
-        __syncwarp();  // the list is reused by the next window or item slot
+        finish_window((total - w0) < L::LIST ? (total - w0) : L::LIST);
+        __syncwarp();  // the list is reused by the next window or slots
       }
     }
   }
