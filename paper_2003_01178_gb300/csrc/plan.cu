@@ -1095,11 +1095,19 @@ __global__ void __launch_bounds__(THREADS, (24 * kWarp) / THREADS > 0 ? (24 * kW
 // query's predicates and aggregate.  Both are put in shared memory by the warp that owns
 // the rows, during the lookups: one region of values per pair and one per fact column the
 // batch finishes with ("staged" columns), all with the same item-major layout (value of
-// item i of thread t at i * THREADS + t).  The lanes of a round finish rows of different
-// threads of the warp, so distinct rows fall in distinct banks; regions are padded by 8
-// words so that one row's values in different regions do too.
+// item i of thread t at i * (THREADS + 16) + t).  The lanes of a round finish rows of
+// different threads of the warp, so distinct rows fall in distinct banks; regions are
+// padded by 8 words so that one row's values in different regions do too.
+//
+// Fact predicates on columns of small range are folded into the row's bitmap the same
+// way: when every fact predicate of the batch lies on at most kMaxPredTags columns, each
+// within kPredTagLen consecutive values, a table per column maps a value to the bitmap
+// of the queries whose predicates on that column it passes.  Finishing then tests no
+// predicate, and rows that fail them never become pairs.
 
 constexpr int kMaxTagPairs = 8;
+constexpr int kMaxPredTags = 2;
+constexpr int kPredTagLen = 256;
 // Tagged-scan blocks resident per SM: two blocks of 512 threads (32 warps) measured
 // faster than three of 256, with the same shared memory left to each block's group
 // accumulators.  A block of 1024 threads has the SM to itself: its shared memory also
@@ -1230,32 +1238,41 @@ struct TagHead {
   int32_t stage_col[CRYS_MAX_COLS];   // staged column s -> fact column (region n_pairs + s)
   int32_t smem_pair;                  // pair whose entries are looked up in shared memory, or -1
   int32_t smem_slots;                 // its entries (its table's capacity)
+  int32_t preds_in_bitmap;            // every fact predicate is folded into the bitmaps
+  int32_t n_ptags;                    // fact columns whose predicates are table lookups
+  int32_t ptag_col[kMaxPredTags];
+  int32_t ptag_base[kMaxPredTags];    // the value of entry 0
+  uint32_t ptag_len[kMaxPredTags];    // entries
+  uint32_t ptag_out[kMaxPredTags];    // the bitmap of a value outside the entries
+  uint32_t ptag[kMaxPredTags][kPredTagLen];  // bitmap of the queries value base + k passes
 };
 
 struct TagArgs : TagHead {
   int32_t desc[CRYS_MAX_PLANS * kDescWords];
 };
 
-// Finishes one (row, query) pair whose dimension verdicts all passed: fact predicates,
-// group code from the pairs' values, aggregate, accumulation.  `vals` holds the value
-// regions (pairs, then staged columns; PVS words apart) and `t` is the row's item-major
-// index in them.
-template <int PVS>
+// Finishes one (row, query) pair whose dimension verdicts all passed: fact predicates
+// (unless PREDS is false: the bitmaps held them), group code from the pairs' values,
+// aggregate, accumulation.  `vals` holds the value regions (pairs, then staged columns;
+// PVS words apart) and `t` is the row's item-major index in them.
+template <int PVS, bool PREDS>
 __device__ __forceinline__ void finish_pair(const DescView<const int32_t> D, const int32_t* vals, int t,
                                             const SharedAcc& acc, int32_t* err) {
   const int32_t* row = vals + t;
   const int32_t xa = row[D[kDAggA] * PVS];
   const int32_t xb = row[D[kDAggB] * PVS];
-  const int32_t x0 = row[D[kDP0Col] * PVS];
-  const int32_t x1 = row[D[kDP1Col] * PVS];
-  bool ok = in_span(x0, D[kDP0Lo], static_cast<uint32_t>(D[kDP0Span])) &
-            in_span(x1, D[kDP1Lo], static_cast<uint32_t>(D[kDP1Span]));
-  const int n_preds = D[kDPreds];
-  for (int f = 2; f < n_preds; ++f) {
-    const int b = kDMorePreds + 3 * (f - 2);
-    ok = ok && in_span(row[D[b] * PVS], D[b + 1], static_cast<uint32_t>(D[b + 2]));
+  if (PREDS) {
+    const int32_t x0 = row[D[kDP0Col] * PVS];
+    const int32_t x1 = row[D[kDP1Col] * PVS];
+    bool ok = in_span(x0, D[kDP0Lo], static_cast<uint32_t>(D[kDP0Span])) &
+              in_span(x1, D[kDP1Lo], static_cast<uint32_t>(D[kDP1Span]));
+    const int n_preds = D[kDPreds];
+    for (int f = 2; f < n_preds; ++f) {
+      const int b = kDMorePreds + 3 * (f - 2);
+      ok = ok && in_span(row[D[b] * PVS], D[b + 1], static_cast<uint32_t>(D[b + 2]));
+    }
+    if (!ok) return;
   }
-  if (!ok) return;
   int32_t gid = 0;
   uint32_t bad = 0;
   auto group = [&](int g) {
@@ -1298,7 +1315,10 @@ __device__ __forceinline__ void finish_pair(const DescView<const int32_t> D, con
 template <int THREADS, int ITEMS>
 struct TagSmem {
   static constexpr int TILE = THREADS * ITEMS;
-  static constexpr int PVS = TILE + 8;  // region stride in words
+  // item slot i of thread t at i * IST + t: a lane's rows of consecutive item slots,
+  // which one finishing list holds, fall 16 banks apart
+  static constexpr int IST = THREADS + 16;
+  static constexpr int PVS = ITEMS * IST + 8;  // region stride in words
   static constexpr int LIST = 256;      // list window of a warp (a round averages a few per lane)
   static constexpr size_t desc_bytes = CRYS_MAX_PLANS * kDescWords * 4;
   static constexpr size_t vals_off = (desc_bytes + 15) / 16 * 16;
@@ -1318,6 +1338,7 @@ __device__ __forceinline__ void tagged_scan_body(const TagHead& a, const int32_t
   constexpr int VEC = ITEMS / 4;
   static_assert(ITEMS <= 8, "a list entry holds a 3-bit item slot and a lane");
   constexpr int PVS = L::PVS;
+  constexpr int IST = L::IST;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int tid = threadIdx.x, lane = tid % kWarp, warp = tid / kWarp;
   const int n_vals = a.n_pairs + a.n_stage;
@@ -1330,7 +1351,11 @@ __device__ __forceinline__ void tagged_scan_body(const TagHead& a, const int32_t
   // this launch has: refuse the work (uniformly in every block) instead of overrunning
   uint32_t dyn_smem;
   asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn_smem));
-  if (a.tile_shape != ((THREADS << 16) | ITEMS) || a.n_stage < 1 || a.n_stage > CRYS_MAX_COLS ||
+  bool ptags_ok = a.n_ptags >= 0 && a.n_ptags <= kMaxPredTags;
+  for (int c = 0; c < kMaxPredTags && ptags_ok; ++c)
+    ptags_ok = c >= a.n_ptags || (a.ptag_len[c] <= static_cast<uint32_t>(kPredTagLen) && a.ptag_col[c] >= 0 &&
+                                  a.ptag_col[c] < CRYS_MAX_COLS);
+  if (a.tile_shape != ((THREADS << 16) | ITEMS) || a.n_stage < 1 || a.n_stage > CRYS_MAX_COLS || !ptags_ok ||
       a.smem_pair >= a.n_pairs || tag_slots < 0 ||
       (a.smem_pair >= 0 && static_cast<uint32_t>(tag_slots) != a.pairs[a.smem_pair].limit) ||
       L::acc_off(n_vals, tag_slots) + static_cast<size_t>(a.shared_groups) * 12 > dyn_smem) {
@@ -1372,6 +1397,17 @@ __device__ __forceinline__ void tagged_scan_body(const TagHead& a, const int32_t
     uint32_t rm[ITEMS];
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) rm[i] = ((live >> i) & 1u) ? a.all_mask : 0u;
+    // fact predicates folded into the bitmaps: one table lookup per column and row
+    for (int c = 0; c < a.n_ptags; ++c) {
+      int32_t x[ITEMS];
+#pragma unroll
+      for (int j = 0; j < VEC; ++j) unpack4(fk_cols.load4(a.ptag_col[c], (j * THREADS + tid) * 4), x + 4 * j);
+#pragma unroll
+      for (int i = 0; i < ITEMS; ++i) {
+        const uint32_t k = static_cast<uint32_t>(x[i]) - static_cast<uint32_t>(a.ptag_base[c]);
+        rm[i] &= k < a.ptag_len[c] ? a.ptag[c][k] : a.ptag_out[c];
+      }
+    }
     __syncwarp();  // the warp is done with the previous tile's values
     // one lookup per pair and row: AND of the dimension verdicts, values kept for groups
     for (int p = 0; p < a.n_pairs; ++p) {
@@ -1398,7 +1434,7 @@ __device__ __forceinline__ void tagged_scan_body(const TagHead& a, const int32_t
 #pragma unroll
       for (int i = 0; i < ITEMS; ++i) {
         rm[i] &= static_cast<uint32_t>(e[i]);
-        vals[p * PVS + i * THREADS + tid] = static_cast<int32_t>(e[i] >> 32);
+        vals[p * PVS + i * IST + tid] = static_cast<int32_t>(e[i] >> 32);
       }
     }
     uint32_t any = 0;
@@ -1411,7 +1447,7 @@ __device__ __forceinline__ void tagged_scan_body(const TagHead& a, const int32_t
 #pragma unroll
       for (int j = 0; j < VEC; ++j) unpack4(fk_cols.load4(a.stage_col[c], (j * THREADS + tid) * 4), x + 4 * j);
 #pragma unroll
-      for (int i = 0; i < ITEMS; ++i) vals[(a.n_pairs + c) * PVS + i * THREADS + tid] = x[i];
+      for (int i = 0; i < ITEMS; ++i) vals[(a.n_pairs + c) * PVS + i * IST + tid] = x[i];
     }
     __syncwarp();  // values of the warp's rows visible to all its lanes
     // Item slots SLOTS at a time: expand each lane's (row, query) pairs of those slots into
@@ -1425,8 +1461,12 @@ __device__ __forceinline__ void tagged_scan_body(const TagHead& a, const int32_t
         if (base + lane < wn) {
           const uint32_t ent = list[base + lane];
           // item-major index of the entry's row: item slot, then the warp's lane
-          const int row = static_cast<int>((ent >> 5) & 7u) * THREADS + warp * kWarp + static_cast<int>(ent & 31u);
-          finish_pair<PVS>(DescView<const int32_t>{desc + (ent >> 8)}, vals, row, acc, a.err);
+          const int row = static_cast<int>((ent >> 5) & 7u) * IST + warp * kWarp + static_cast<int>(ent & 31u);
+          const DescView<const int32_t> D{desc + (ent >> 8)};
+          if (a.preds_in_bitmap)
+            finish_pair<PVS, false>(D, vals, row, acc, a.err);
+          else
+            finish_pair<PVS, true>(D, vals, row, acc, a.err);
         }
       }
     };
@@ -1944,6 +1984,53 @@ bool tag_batch(const crys_plan* plans, const DevQuery* q, int n, TagBatch* tb) {
     }
     return region_of[c];
   };
+  // fact predicates folded into the bitmaps, when each column's predicates in the batch
+  // span at most kPredTagLen values and at most kMaxPredTags columns have any
+  // (queries that no row can satisfy are left out: their bit is never set)
+  S.preds_in_bitmap = 1;
+  S.n_ptags = 0;
+  int64_t plo[CRYS_MAX_COLS], phi[CRYS_MAX_COLS];
+  uint32_t pq[CRYS_MAX_COLS];
+  for (int c = 0; c < CRYS_MAX_COLS; ++c) {
+    plo[c] = INT64_MAX;
+    phi[c] = INT64_MIN;
+    pq[c] = 0;
+  }
+  for (int qi = 0; qi < n; ++qi) {
+    if (q[qi].never) continue;
+    for (int f = 0; f < q[qi].n_preds; ++f) {
+      const int c = q[qi].pred_col[f];
+      plo[c] = q[qi].pred_lo[f] < plo[c] ? q[qi].pred_lo[f] : plo[c];
+      phi[c] = q[qi].pred_hi[f] > phi[c] ? q[qi].pred_hi[f] : phi[c];
+      pq[c] |= 1u << qi;
+    }
+  }
+  for (int c = 0; c < CRYS_MAX_COLS && S.preds_in_bitmap; ++c) {
+    if (!pq[c]) continue;
+    if (S.n_ptags == kMaxPredTags || phi[c] - plo[c] + 1 > kPredTagLen) {
+      S.preds_in_bitmap = 0;
+      break;
+    }
+    const int t = S.n_ptags++;
+    S.ptag_col[t] = c;
+    S.ptag_base[t] = static_cast<int32_t>(plo[c]);
+    S.ptag_len[t] = static_cast<uint32_t>(phi[c] - plo[c] + 1);
+    S.ptag_out[t] = everyone & ~pq[c];
+    for (int k = 0; k < kPredTagLen; ++k) {
+      uint32_t bits = S.ptag_out[t];
+      const int64_t v = plo[c] + k;
+      if (k < static_cast<int>(S.ptag_len[t]))
+        for (int qi = 0; qi < n; ++qi) {
+          if (!((pq[c] >> qi) & 1u)) continue;
+          bool ok = true;
+          for (int f = 0; f < q[qi].n_preds; ++f)
+            if (q[qi].pred_col[f] == c) ok = ok && q[qi].pred_lo[f] <= v && v <= q[qi].pred_hi[f];
+          if (ok) bits |= 1u << qi;
+        }
+      S.ptag[t][k] = k < static_cast<int>(S.ptag_len[t]) ? bits : 0u;
+    }
+  }
+  if (!S.preds_in_bitmap) S.n_ptags = 0;
   // descriptors
   S.n_queries = n;
   S.all_mask = 0;
@@ -1954,17 +2041,19 @@ bool tag_batch(const crys_plan* plans, const DevQuery* q, int n, TagBatch* tb) {
     if (!Q.never) S.all_mask |= 1u << qi;
     // fact predicates: the first two in fixed fields (an unused one always passes: any
     // value of the aggregate column lies in [0, 0 + 2^32 - 1]), the rest in a list
-    D[kDPreds] = Q.n_preds;
-    const int32_t pc[2] = {Q.n_preds > 0 ? Q.pred_col[0] : Q.agg_a, Q.n_preds > 1 ? Q.pred_col[1] : Q.agg_a};
-    const int32_t pl[2] = {Q.n_preds > 0 ? Q.pred_lo[0] : 0, Q.n_preds > 1 ? Q.pred_lo[1] : 0};
-    const uint32_t ps[2] = {Q.n_preds > 0 ? Q.pred_span[0] : 0xFFFFFFFFu, Q.n_preds > 1 ? Q.pred_span[1] : 0xFFFFFFFFu};
+    // (none when the bitmaps hold them: finishing then reads no predicate field)
+    const int np = S.preds_in_bitmap ? 0 : Q.n_preds;
+    D[kDPreds] = np;
+    const int32_t pc[2] = {np > 0 ? Q.pred_col[0] : Q.agg_a, np > 1 ? Q.pred_col[1] : Q.agg_a};
+    const int32_t pl[2] = {np > 0 ? Q.pred_lo[0] : 0, np > 1 ? Q.pred_lo[1] : 0};
+    const uint32_t ps[2] = {np > 0 ? Q.pred_span[0] : 0xFFFFFFFFu, np > 1 ? Q.pred_span[1] : 0xFFFFFFFFu};
     D[kDP0Col] = region(pc[0]);
     D[kDP0Lo] = pl[0];
     D[kDP0Span] = static_cast<int32_t>(ps[0]);
     D[kDP1Col] = region(pc[1]);
     D[kDP1Lo] = pl[1];
     D[kDP1Span] = static_cast<int32_t>(ps[1]);
-    for (int f = 2; f < Q.n_preds; ++f) {
+    for (int f = 2; f < np; ++f) {
       D[kDMorePreds + 3 * (f - 2)] = region(Q.pred_col[f]);
       D[kDMorePreds + 3 * (f - 2) + 1] = Q.pred_lo[f];
       D[kDMorePreds + 3 * (f - 2) + 2] = static_cast<int32_t>(Q.pred_span[f]);
@@ -2045,8 +2134,11 @@ int64_t assign_accumulators(TagArgs& S, const DevQuery* q, size_t budget) {
   return used;
 }
 
-// Shared memory of one tagged-scan block.
-constexpr size_t tag_share(int threads) { return (220u * 1024u) / tag_blocks_per_sm(threads); }
+// Shared memory of one tagged-scan block: a block alone on its SM takes all but its
+// static head of the 227 KB a block may have; two blocks take 110 KB each.
+constexpr size_t tag_share(int threads) { return tag_blocks_per_sm(threads) == 1 ? 224u * 1024u : 110u * 1024u; }
+static_assert(224u * 1024u + sizeof(TagHead) <= 227u * 1024u, "one block's shared memory");
+static_assert(2 * (110u * 1024u + sizeof(TagHead) + 1024u) <= 228u * 1024u, "two blocks' shared memory");
 
 // The pair whose entries a block of this shape looks up in shared memory: the smallest
 // table of at most kTagSmemBytes, in blocks that have their SM to itself (-1: none).

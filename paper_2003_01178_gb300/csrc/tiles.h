@@ -23,7 +23,7 @@ constexpr TileShape kTiles[CRYS_NUM_OPS][kMaxVariants] = {
     /* PLAN        */ {{256, 8}, {512, 8}, {512, 4}, {128, 4}},
     /* SHARED_SCAN */ {{256, 4}, {256, 8}, {128, 8}, {128, 4}},
     /* SORT        */ {{256, 32}, {256, 24}, {512, 16}, {256, 16}},
-    /* TAGGED_SCAN */ {{512, 4}, {256, 4}, {1024, 4}, {256, 8}},
+    /* TAGGED_SCAN */ {{1024, 4}, {256, 4}, {512, 4}, {256, 8}},
 };
 
 constexpr int kNumVariants[CRYS_NUM_OPS] = {4, 4, 4, 4, 4, 4, 4};

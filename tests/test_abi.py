@@ -39,11 +39,11 @@ def test_strerror_and_tiles(crys):
         v = crys.crys_tile_variants(op)
         assert 1 <= len(v) <= 4 and all(t % 32 == 0 and i > 0 for t, i in v)
     assert crys.crys_tile_variants(0)[3] == (128, 4)      # the paper's tile shape is available
-    # the tagged scan has shapes of its own; its default runs two 512-thread blocks per SM,
-    # and one shape a 1024-thread block per SM (the smallest table's entries in shared
-    # memory); a list entry holds a 3-bit item slot, so at most 8 items per thread
+    # the tagged scan has shapes of its own; its default runs one 1024-thread block per SM
+    # (the smallest table's entries in shared memory), another two 512-thread blocks; a
+    # list entry holds a 3-bit item slot, so at most 8 items per thread
     tagged = crys.crys_tile_variants(crys.OP_TAGGED_SCAN)
-    assert crys.NUM_OPS == 7 and tagged[0] == (512, 4) and (1024, 4) in tagged
+    assert crys.NUM_OPS == 7 and tagged[0] == (1024, 4) and (512, 4) in tagged
     assert all(i <= 8 and t <= 1024 for t, i in tagged)
     with pytest.raises(crys.CrystalError):
         crys.crys_set_tile(0, 99)

@@ -122,7 +122,7 @@ def test_replayed_scan_follows_a_new_tile_shape(store, orc):
     try:
         crys.crys_set_tile(crys.OP_TAGGED_SCAN, 0)
         assert rep.launch(mine, 0, 100_000, list(range(10)))
-        crys.crys_set_tile(crys.OP_TAGGED_SCAN, 2)      # one 1024-thread block per SM
+        crys.crys_set_tile(crys.OP_TAGGED_SCAN, 2)      # two 512-thread blocks per SM
         assert rep.launch(mine, 100_000, 200_000, [])
         crys.crys_set_tile(crys.OP_TAGGED_SCAN, 1)
         assert rep.launch(mine, 200_000, n, [])

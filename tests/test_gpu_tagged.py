@@ -215,3 +215,37 @@ def test_tagged_every_fact_column_finishes(crys, orc, world, variant):
         assert np.array_equal(s.cpu().numpy(), rs) and np.array_equal(c.cpu().numpy(), rc)
     crys.check_device_errors()
     crys.crys_set_tile(crys.OP_TAGGED_SCAN, 0)
+
+
+_PRED_CASES = {
+    # two columns of small range: folded into the bitmaps (one table per column); two
+    # predicates of one query on one column, a range reaching below the column's values,
+    # one no row passes (b <= 10), one no row can satisfy (lo > hi), and on b a union of
+    # ranges 256 values wide
+    "folded": [[(2, 10, 40), (2, 20, 60)], [(3, 1, 9)], [(2, -5, 3)], [(3, 11, 20)], [(2, 30, 20)],
+               [(2, 1, 50), (3, 0, 10)], [(3, -235, 5)], []],
+    # the same with three predicated columns: finishing tests them
+    "three_columns": [[(2, 10, 40), (2, 20, 60)], [(3, 1, 9)], [(1, 0, 31)], [(2, 30, 20)], []],
+    # a column whose predicates span 257 values: finishing tests them
+    "wide": [[(0, 0, 256)], [(3, 1, 9)], [(2, 5, 45)], []],
+}
+
+
+@pytest.mark.parametrize("variant", [0, 2])
+@pytest.mark.parametrize("case", sorted(_PRED_CASES))
+def test_tagged_fact_predicates(crys, orc, world, variant, case):
+    """Fact predicates in the bitmaps or in finishing, each query against the oracle."""
+    crys.crys_set_tile(crys.OP_TAGGED_SCAN, variant)
+    d0, t0 = world["d0"], world["t0"]
+    qs = []
+    for i, preds in enumerate(_PRED_CASES[case]):
+        joins = [((0, t0, 16, X, []),
+                  {"fk_col": 0, "keys": d0["key"], "preds": [], "group": d0["x"], "card": 16})] if i % 2 else []
+        qs.append((joins, preds, ("mul", 4, 3) if i % 3 else ("sum", 4, None)))
+    plans, outs = _plans(crys, qs)
+    _tagged(crys, world, plans, [(0, 40_000), (40_000, N)])
+    for (joins, preds, agg), (s, c) in zip(qs, outs):
+        rs, rc = orc.run_plan_raw(world["fact"], preds, [o for _, o in joins], agg)
+        assert np.array_equal(s.cpu().numpy(), rs) and np.array_equal(c.cpu().numpy(), rc)
+    crys.check_device_errors()
+    crys.crys_set_tile(crys.OP_TAGGED_SCAN, 0)
