@@ -1121,7 +1121,9 @@ constexpr int kMaxTagEntries = CRYS_MAX_PLANS * CRYS_MAX_JOINS;
 // queries they finish, so distinct queries fall in distinct banks and equal ones share a
 // broadcast: one wavefront per field read.  Unused predicates and groups hold entries
 // that always pass, so every lane runs the same instructions whatever query it finishes.
-constexpr int kDescWords = 54;
+// What every pair reads is also packed into few words (kDPack, kDGroupW): shared-memory
+// wavefronts, not instructions, bound finishing.
+constexpr int kDescWords = 56;
 enum DescField : int {
   kDAggA = 0, kDAggB = 1,                     // aggregate operands (value regions)
   kDAccMode = 2, kDAccOff = 3,                // shared-memory accumulators (offset) or global
@@ -1129,12 +1131,17 @@ enum DescField : int {
   kDP1Col = 7, kDP1Lo = 8, kDP1Span = 9,      // fact predicate 1
   kDPreds = 10, kDGroups = 11,                // fact predicates, grouped joins
   kDMulAB = 12, kDCoefA = 13, kDCoefB = 14,   // val = a*b, or ca*a + cb*b
+  // region of a | region of b << 5 | operator << 10 (0 a, 1 a*b, 2 a-b, 3 a+b) |
+  // grouped joins << 12 | global accumulators << 15
+  kDPack = 15,
   kDGroup0 = 16,      // 4 grouped joins of 4 words: pair << 8 | shift, mask, card, stride
   kDSums = 32,        // output pointers: sums (2 words), then counts (2 words)
   kDCounts = 34,
   kDMorePreds = 36,   // fact predicates 2..7: region, lo, span
+  kDGroupW = 54,      // grouped joins 0, 1: pair | shift << 4 | mask bits << 9
 };
-static_assert(kDMorePreds + 3 * (CRYS_MAX_PREDS - 2) <= kDescWords, "descriptor fields");
+static_assert(kDMorePreds + 3 * (CRYS_MAX_PREDS - 2) <= kDGroupW && kDGroupW + 2 <= kDescWords, "descriptor fields");
+static_assert(kMaxTagPairs + CRYS_MAX_COLS <= 32, "a value region index fits 5 bits");
 
 // Field access to one query's descriptor in the field-major layout.
 template <typename T>
@@ -1259,8 +1266,9 @@ template <int PVS, bool PREDS>
 __device__ __forceinline__ void finish_pair(const DescView<const int32_t> D, const int32_t* vals, int t,
                                             const SharedAcc& acc, int32_t* err) {
   const int32_t* row = vals + t;
-  const int32_t xa = row[D[kDAggA] * PVS];
-  const int32_t xb = row[D[kDAggB] * PVS];
+  const uint32_t pk = static_cast<uint32_t>(D[kDPack]);
+  const int32_t xa = row[(pk & 31u) * PVS];
+  const int32_t xb = row[((pk >> 5) & 31u) * PVS];
   if (PREDS) {
     const int32_t x0 = row[D[kDP0Col] * PVS];
     const int32_t x1 = row[D[kDP1Col] * PVS];
@@ -1282,18 +1290,26 @@ __device__ __forceinline__ void finish_pair(const DescView<const int32_t> D, con
     bad |= static_cast<uint32_t>(code >= static_cast<uint32_t>(D[kDGroup0 + 4 * g + 2]));
     gid += static_cast<int32_t>(code) * D[kDGroup0 + 4 * g + 3];
   };
-  group(0);
-  group(1);
-  const int n_groups = D[kDGroups];
+  auto group_packed = [&](int g) {  // grouped joins 0 and 1 from their packed words
+    const uint32_t w = static_cast<uint32_t>(D[kDGroupW + g]);
+    const uint32_t mb = (w >> 9) & 63u;
+    const uint32_t mask = mb >= 32u ? 0xFFFFFFFFu : ((1u << mb) - 1u);
+    const uint32_t code = (static_cast<uint32_t>(row[(w & 15u) * PVS]) >> ((w >> 4) & 31u)) & mask;
+    bad |= static_cast<uint32_t>(code >= static_cast<uint32_t>(D[kDGroup0 + 4 * g + 2]));
+    gid += static_cast<int32_t>(code) * D[kDGroup0 + 4 * g + 3];
+  };
+  group_packed(0);
+  group_packed(1);
+  const int n_groups = static_cast<int>((pk >> 12) & 7u);
   for (int g = 2; g < n_groups; ++g) group(g);
   if (bad) {
     set_error(err, CRYS_DEV_BAD_GROUP);
     return;
   }
-  const int64_t prod = static_cast<int64_t>(xa) * xb;
-  const int64_t lin = static_cast<int64_t>(xa) * D[kDCoefA] + static_cast<int64_t>(xb) * D[kDCoefB];
-  const int64_t val = D[kDMulAB] ? prod : lin;
-  if (D[kDAccMode] != kAccGlobal) {
+  const uint32_t op = (pk >> 10) & 3u;
+  const int64_t a64 = xa, b64 = xb;
+  const int64_t val = op == 1u ? a64 * b64 : a64 + (op == 2u ? -b64 : (op == 3u ? b64 : int64_t{0}));
+  if (!((pk >> 15) & 1u)) {
     const int slot = D[kDAccOff] + gid;
     shared_add_u64(acc.sums + slot, static_cast<unsigned long long>(val));
     atomicAdd(acc.counts + slot, 1u);
@@ -2070,6 +2086,9 @@ bool tag_batch(const crys_plan* plans, const DevQuery* q, int n, TagBatch* tb) {
       const DevJoin& J = Q.joins[j];
       if (J.card <= 0) continue;
       D[kDGroup0 + 4 * ng] = (pair_of[qi][j] << 8) | static_cast<int32_t>(J.gshift);
+      if (ng < 2)
+        D[kDGroupW + ng] = pair_of[qi][j] | static_cast<int32_t>(J.gshift << 4) |
+                           (__builtin_popcount(J.gmask) << 9);
       D[kDGroup0 + 4 * ng + 1] = static_cast<int32_t>(J.gmask);
       D[kDGroup0 + 4 * ng + 2] = J.card;
       D[kDGroup0 + 4 * ng + 3] = J.stride;
@@ -2082,6 +2101,8 @@ bool tag_batch(const crys_plan* plans, const DevQuery* q, int n, TagBatch* tb) {
     D[kDMulAB] = Q.agg_op == CRYS_AGG_A_MUL_B ? 1 : 0;
     D[kDCoefA] = Q.agg_op == CRYS_AGG_A_MUL_B ? 0 : 1;
     D[kDCoefB] = Q.agg_op == CRYS_AGG_A_SUB_B ? -1 : (Q.agg_op == CRYS_AGG_A_ADD_B ? 1 : 0);
+    const int32_t op = Q.agg_op == CRYS_AGG_A_MUL_B ? 1 : (Q.agg_op == CRYS_AGG_A_SUB_B ? 2 : (Q.agg_op == CRYS_AGG_A_ADD_B ? 3 : 0));
+    D[kDPack] = D[kDAggA] | (D[kDAggB] << 5) | (op << 10) | (ng << 12);  // accumulators: assign_accumulators
     const uint64_t sp = reinterpret_cast<uint64_t>(Q.sums), cp = reinterpret_cast<uint64_t>(Q.counts);
     D[kDSums] = static_cast<int32_t>(static_cast<uint32_t>(sp));
     D[kDSums + 1] = static_cast<int32_t>(static_cast<uint32_t>(sp >> 32));
@@ -2129,8 +2150,12 @@ int64_t assign_accumulators(TagArgs& S, const DevQuery* q, size_t budget) {
   }
   S.shared_groups = static_cast<int32_t>(used);
   S.global_mask = 0;
-  for (int qi = 0; qi < S.n_queries; ++qi)
-    if (S.desc[kDAccMode * CRYS_MAX_PLANS + qi] == kAccGlobal) S.global_mask |= 1u << qi;
+  for (int qi = 0; qi < S.n_queries; ++qi) {
+    const DescView<int32_t> D{S.desc + qi};
+    const bool global = D[kDAccMode] == kAccGlobal;
+    if (global) S.global_mask |= 1u << qi;
+    D[kDPack] = (D[kDPack] & ~(1 << 15)) | (global ? 1 << 15 : 0);
+  }
   return used;
 }
 
