@@ -328,7 +328,10 @@ int crys_run_plans(const crys_table* fact, const crys_plan* plans, int32_t n_pla
  * q set when plan q does not join through the pair, or joins it and the row passes all
  * of q's bit-field predicates on it).  The fact scan ANDs one entry per pair into each
  * row's bitmap and finishes only the (row, plan) pairs still set: fact predicates, group
- * code, aggregate.  Results are those of crys_run_plans, and so is every argument rule.
+ * code, aggregate.  When the batch's fact predicates lie on at most two columns, each
+ * within 256 consecutive values, they too become bitmaps (a per-batch table per column,
+ * looked up once per row) and finishing tests none.  Results are those of
+ * crys_run_plans, and so is every argument rule.
  *   crys_run_plans_tagged_bytes  scratch bytes the bitmaps of this batch need; 0 when the
  *                                batch cannot be tagged.
  *   scratch       device memory, 16-byte aligned, rebuilt by every call.  With scratch

@@ -2123,14 +2123,39 @@ void place_annotations(TagBatch& tb, unsigned char* scratch) {
   }
 }
 
-// Group accumulators in shared memory for as many queries as fit in `budget` bytes
-// (smallest group counts first: they have the most rows per group, where global atomics
-// would contend most); the rest accumulate with global atomics.  Returns the groups held.
+// Expected fraction of fact rows a query keeps, from its dimension predicates on bit
+// fields, taking field values as uniform (1 where it cannot tell, 0 when no row can
+// qualify).  Only orders queries for the shared accumulators; no result depends on it.
+double kept_fraction(const DevQuery& Q) {
+  if (Q.never) return 0.0;
+  double f = 1.0;
+  for (int j = 0; j < Q.n_joins; ++j)
+    for (int k = 0; k < Q.joins[j].n_fp; ++k) {
+      const uint32_t mask = Q.joins[j].fp_mask[k];
+      if (mask == 0xFFFFFFFFu) continue;
+      const int64_t lo = Q.joins[j].fp_lo[k] < 0 ? 0 : Q.joins[j].fp_lo[k];
+      const int64_t hi = Q.joins[j].fp_hi[k] > static_cast<int64_t>(mask) ? mask : Q.joins[j].fp_hi[k];
+      f *= hi < lo ? 0.0 : static_cast<double>(hi - lo + 1) / (static_cast<double>(mask) + 1.0);
+    }
+  return f;
+}
+
+// Group accumulators in shared memory for as many queries as fit in `budget` bytes, the
+// queries with the most expected rows per group first (their global atomics would be the
+// most frequent and contend most); the rest accumulate with global atomics.  Returns the
+// groups held.
 int64_t assign_accumulators(TagArgs& S, const DevQuery* q, size_t budget) {
   int order[CRYS_MAX_PLANS];
-  for (int qi = 0; qi < S.n_queries; ++qi) order[qi] = qi;
+  double density[CRYS_MAX_PLANS];
+  for (int qi = 0; qi < S.n_queries; ++qi) {
+    order[qi] = qi;
+    density[qi] = kept_fraction(q[qi]) / static_cast<double>(q[qi].groups < 1 ? 1 : q[qi].groups);
+  }
+  auto before = [&](int x, int y) {  // x goes first
+    return density[x] != density[y] ? density[x] > density[y] : q[x].groups < q[y].groups;
+  };
   for (int i = 1; i < S.n_queries; ++i)
-    for (int j = i; j > 0 && q[order[j]].groups < q[order[j - 1]].groups; --j) {
+    for (int j = i; j > 0 && before(order[j], order[j - 1]); --j) {
       const int t = order[j];
       order[j] = order[j - 1];
       order[j - 1] = t;
