@@ -134,7 +134,8 @@ __device__ __forceinline__ void unpack4(int4 q, int32_t* dst) {
 }
 
 // Probes one table for this thread's ITEMS rows: all first-slot reads are issued before
-// any is resolved, and continuations a probing step at a time for all rows together.  Returns the bitmap of rows whose key was found; values in `value`.
+// any is resolved.  (Continuations go item by item here: resolving them together, as the
+// probe kernel does, costs this kernel 20 more registers and half its resident blocks.)  Returns the bitmap of rows whose key was found; values in `value`.
 template <int ITEMS>
 __device__ __forceinline__ uint32_t probe_items(const uint64_t* slots, const HashFn& hf,
                                                 const int32_t (&key)[ITEMS], uint32_t live,
@@ -161,9 +162,14 @@ __device__ __forceinline__ uint32_t probe_items(const uint64_t* slots, const Has
     h[i] = hash_slot(key[i], hf);
     slot[i] = ((live >> i) & 1u) && hash_may_hold(key[i], hf) ? ld_slot(slots + h[i], pol) : kEmptySlot;
   }
+  uint32_t found = 0;
 #pragma unroll
-  for (int i = 0; i < ITEMS; ++i) value[i] = 0;
-  return hash_resolve_all<ITEMS>(slots, hf, h, slot, key, live, value, pol);
+  for (int i = 0; i < ITEMS; ++i) {
+    value[i] = 0;
+    if (((live >> i) & 1u) && hash_resolve(slots, hf, h[i], slot[i], key[i], &value[i], pol))
+      found |= 1u << i;
+  }
+  return found;
 }
 
 // Range test lo <= v <= hi as one unsigned comparison (span = hi - lo).
@@ -1021,10 +1027,14 @@ __global__ void __launch_bounds__(THREADS, (24 * kWarp) / THREADS > 0 ? (24 * kW
         if (d >= a.n_probes) break;
         const ProbeSpec& P = a.probes[d];
         int32_t value[ITEMS];
+        uint32_t found = 0;
 #pragma unroll
-        for (int i = 0; i < ITEMS; ++i) value[i] = 0;
-        const uint32_t found =
-            hash_resolve_all<ITEMS>(P.slots, P.hash, h[dd], slot[dd], key[dd], live, value, pol_table);
+        for (int i = 0; i < ITEMS; ++i) {
+          value[i] = 0;
+          if (((live >> i) & 1u) &&
+              hash_resolve(P.slots, P.hash, h[dd][i], slot[dd][i], key[dd][i], &value[i], pol_table))
+            found |= 1u << i;
+        }
         pf[d * THREADS + tid] = found;
 #pragma unroll
         for (int j = 0; j < VEC; ++j)
@@ -1425,14 +1435,12 @@ __device__ __forceinline__ void tagged_scan_body(const TagHead& a, const int32_t
       }
     }
     __syncwarp();  // the warp is done with the previous tile's values
-    // one lookup per pair and row: AND of the dimension verdicts, values kept for groups
-    for (int p = 0; p < a.n_pairs; ++p) {
-      const TagScanPair& P = a.pairs[p];
-      int32_t key[ITEMS];
-#pragma unroll
-      for (int j = 0; j < VEC; ++j) unpack4(fk_cols.load4(P.fk_col, (j * THREADS + tid) * 4), key + 4 * j);
-      uint64_t e[ITEMS];
-      if (p == a.smem_pair) {
+    // one lookup per pair and row: AND of the dimension verdicts, values kept for groups.
+    // Two pairs at a time: the second pair's lookups go out before the first pair's
+    // verdicts are in (gated only on what the row had before both), so a warp waits for
+    // one L2 round trip per two pairs.
+    auto lookup = [&](const TagScanPair& P, bool in_smem, const int32_t (&key)[ITEMS], uint64_t (&e)[ITEMS]) {
+      if (in_smem) {
 #pragma unroll
         for (int i = 0; i < ITEMS; ++i)
           e[i] = (rm[i] && static_cast<uint32_t>(key[i]) < P.limit) ? stag[key[i]] : static_cast<uint64_t>(P.nonjoin);
@@ -1447,10 +1455,31 @@ __device__ __forceinline__ void tagged_scan_body(const TagHead& a, const int32_t
           e[i] = (rm[i] && static_cast<uint32_t>(key[i]) < P.limit) ? ld_tag_bypass(P.ann + key[i], pol_table)
                                                                     : static_cast<uint64_t>(P.nonjoin);
       }
+    };
+    for (int p = 0; p < a.n_pairs; p += 2) {
+      const bool two = p + 1 < a.n_pairs;
+      int32_t key0[ITEMS], key1[ITEMS];
+      uint64_t e0[ITEMS], e1[ITEMS];
+#pragma unroll
+      for (int j = 0; j < VEC; ++j) unpack4(fk_cols.load4(a.pairs[p].fk_col, (j * THREADS + tid) * 4), key0 + 4 * j);
+      if (two) {
+#pragma unroll
+        for (int j = 0; j < VEC; ++j)
+          unpack4(fk_cols.load4(a.pairs[p + 1].fk_col, (j * THREADS + tid) * 4), key1 + 4 * j);
+      }
+      lookup(a.pairs[p], p == a.smem_pair, key0, e0);
+      if (two) lookup(a.pairs[p + 1], p + 1 == a.smem_pair, key1, e1);
 #pragma unroll
       for (int i = 0; i < ITEMS; ++i) {
-        rm[i] &= static_cast<uint32_t>(e[i]);
-        vals[p * PVS + i * IST + tid] = static_cast<int32_t>(e[i] >> 32);
+        rm[i] &= static_cast<uint32_t>(e0[i]);
+        vals[p * PVS + i * IST + tid] = static_cast<int32_t>(e0[i] >> 32);
+      }
+      if (two) {
+#pragma unroll
+        for (int i = 0; i < ITEMS; ++i) {
+          rm[i] &= static_cast<uint32_t>(e1[i]);
+          vals[(p + 1) * PVS + i * IST + tid] = static_cast<int32_t>(e1[i] >> 32);
+        }
       }
     }
     uint32_t any = 0;
