@@ -3,7 +3,9 @@
 Each operator is compiled for a few tile shapes (``crys_tile_variants``).  ``tune`` times
 every variant of an operator on a caller-supplied launch (CUDA events, warm-up first,
 median of several runs) and selects the fastest with ``crys_set_tile``; ``save`` / ``load``
-persist the choice per device name as JSON so later processes start with it.
+persist the choice per device name as JSON so later processes start with it.  The choice
+is stored as the tile shape, not the variant's index, so a library whose variant list
+changed still finds it (or ignores it when that shape is no longer compiled).
 """
 from __future__ import annotations
 
@@ -54,14 +56,15 @@ def save(path: str = DEFAULT_PATH) -> None:
     if os.path.exists(path):
         with open(path) as f:
             data = json.load(f)
-    data[_key()] = {OP_NAMES[op]: crys_get_tile(op) for op in range(len(OP_NAMES))}
+    data[_key()] = {OP_NAMES[op]: list(crys_tile_variants(op)[crys_get_tile(op)]) for op in range(len(OP_NAMES))}
     os.makedirs(os.path.dirname(path), exist_ok=True)
     with open(path, "w") as f:
         json.dump(data, f, indent=1)
 
 
 def load(path: str = DEFAULT_PATH) -> bool:
-    """Applies the persisted choice for this device, if any."""
+    """Applies the persisted choice for this device, if any.  A stored shape that is not
+    among an operator's variants (or an entry in another form) is ignored."""
     if not os.path.exists(path):
         return False
     with open(path) as f:
@@ -69,6 +72,10 @@ def load(path: str = DEFAULT_PATH) -> bool:
     if not data:
         return False
     for op, name in enumerate(OP_NAMES):
-        if name in data:
-            crys_set_tile(op, int(data[name]))
+        shape = data.get(name)
+        if not isinstance(shape, list) or len(shape) != 2:
+            continue
+        variants = [list(v) for v in crys_tile_variants(op)]
+        if shape in variants:
+            crys_set_tile(op, variants.index(shape))
     return True

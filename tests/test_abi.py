@@ -179,3 +179,32 @@ def test_debug_stall_arguments(crys):
     assert L.crys_debug_stall(crys.OP_SELECT, -1, 1_000_000) == crys.EINVAL
     assert L.crys_debug_stall(crys.OP_SELECT, 1, 10) == crys.EINVAL
     assert L.crys_debug_stall(crys.OP_SORT, 1, 3_000_000_000) == crys.EINVAL
+
+
+def test_tuner_persists_tile_shapes(crys, tmp_path, monkeypatch):
+    """The autotuner stores each operator's choice as a tile shape: loading finds that
+    shape's variant even if the variant list was reordered, and ignores a shape that is
+    no longer compiled or an entry in another form (no GPU needed: choices are host state)."""
+    import json
+    from paper_2003_01178_gb300 import tuner
+    monkeypatch.setattr(tuner, "_key", lambda: "test-device")
+    path = str(tmp_path / "tiles.json")
+    op = crys.OP_TAGGED_SCAN
+    variants = crys.crys_tile_variants(op)
+    try:
+        crys.crys_set_tile(op, 2)
+        tuner.save(path)
+        stored = json.load(open(path))["test-device"]
+        assert stored[crys.OP_NAMES[op]] == list(variants[2])
+        crys.crys_set_tile(op, 0)
+        assert tuner.load(path) and crys.crys_get_tile(op) == 2
+        stored[crys.OP_NAMES[op]] = [96, 3]                 # not a compiled shape
+        stored[crys.OP_NAMES[crys.OP_SELECT]] = 1            # an index (another form)
+        json.dump({"test-device": stored}, open(path, "w"))
+        crys.crys_set_tile(op, 1)
+        crys.crys_set_tile(crys.OP_SELECT, 3)
+        assert tuner.load(path)
+        assert crys.crys_get_tile(op) == 1 and crys.crys_get_tile(crys.OP_SELECT) == 3
+    finally:
+        for o in range(crys.NUM_OPS):
+            crys.crys_set_tile(o, 0)
