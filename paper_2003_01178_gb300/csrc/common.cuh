@@ -170,11 +170,18 @@ __device__ __forceinline__ void st_relaxed_u32(uint32_t* p, uint32_t v) {
 
 // ---------------------------------------------------------------- hashing
 
-// Home slot of a key: ((uint32)key * mult >> shift) & mask.  Multiplicative (Fibonacci)
-// hashing uses mult = 2654435769 (2^32/phi) and shift = 32 - log2(capacity); identity
-// hashing (key mod capacity) uses mult = 1, shift = 0.
+// Home slot of a key: (hi32(key * mult) >> shift) & mask, where hi32 is bits 32..63 of
+// the 64-bit product (uint32)key * mult, formed as key * mult_hi + umulhi(key, mult_lo).
+// Multiplicative (Fibonacci) hashing takes the top log2(capacity) bits of the product with
+// mult = 0x9E3779B97F4A7C15 (the integer part of 2^64/phi, odd), shift = 32 - log2(capacity).
+// With the 32-bit constant 2654435769 (2^32/phi) instead, dense keys 0..n-1 cluster at
+// some sizes: a lookup examines 2.3 slots on average at n = 2^22 (1.7 at 2^21, 1.3 at
+// 2^20) against 1.0 with the 64-bit product at every n from 2^10 to 2^27; random keys
+// examine the 1.5 of linear probing at 50% fill either way.  Identity hashing (key mod
+// capacity) uses mult = 2^32 (mult_hi = 1, mult_lo = 0), shift = 0.
 struct HashFn {
-  uint32_t mult, shift, mask;
+  uint32_t mult_hi, mult_lo;
+  uint32_t shift, mask;
   uint32_t limit;  // keys >= limit (as unsigned) are absent without reading a slot
   uint32_t steps;  // further slots a lookup may examine after the home slot
 };
@@ -184,7 +191,8 @@ __host__ __device__ __forceinline__ HashFn make_hash(int32_t kind, int64_t capac
   HashFn h;
   if (kind == CRYS_HASH_DIRECT) {
     // the slot of key k is k itself: a key is in its slot or absent
-    h.mult = 1u;
+    h.mult_hi = 1u;
+    h.mult_lo = 0u;
     h.shift = 0u;
     h.mask = 0xFFFFFFFFu;
     h.limit = static_cast<uint32_t>(capacity);
@@ -197,17 +205,20 @@ __host__ __device__ __forceinline__ HashFn make_hash(int32_t kind, int64_t capac
   h.limit = 0xFFFFFFFFu;  // key -1 is the empty marker and never stored
   h.steps = h.mask;
   if (kind == CRYS_HASH_IDENT) {
-    h.mult = 1u;
+    h.mult_hi = 1u;
+    h.mult_lo = 0u;
     h.shift = 0u;
   } else {
-    h.mult = 2654435769u;
+    h.mult_hi = 0x9E3779B9u;
+    h.mult_lo = 0x7F4A7C15u;
     h.shift = 32u - log2cap;
   }
   return h;
 }
 
 __device__ __forceinline__ uint32_t hash_slot(int32_t key, const HashFn& f) {
-  return ((static_cast<uint32_t>(key) * f.mult) >> f.shift) & f.mask;
+  const uint32_t k = static_cast<uint32_t>(key);
+  return ((k * f.mult_hi + __umulhi(k, f.mult_lo)) >> f.shift) & f.mask;
 }
 
 // Whether a key can be in the table at all (direct tables: 0 <= key < capacity).

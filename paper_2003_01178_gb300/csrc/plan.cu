@@ -142,7 +142,7 @@ __device__ __forceinline__ uint32_t probe_items(const uint64_t* slots, const Has
                                                 int32_t (&value)[ITEMS], uint64_t pol) {
   uint32_t h[ITEMS];
   uint64_t slot[ITEMS];
-  if (hf.steps == 0u && hf.mult == 1u && hf.shift == 0u && hf.mask == 0xFFFFFFFFu) {
+  if (hf.steps == 0u && hf.mult_hi == 1u && hf.mult_lo == 0u && hf.shift == 0u && hf.mask == 0xFFFFFFFFu) {
     // direct table (uniform branch): a key below the capacity is in slot `key` or
     // absent, one read per row
     uint32_t found = 0;
@@ -1820,7 +1820,7 @@ int launch_plan(PlanArgs& a, cudaStream_t s) {
   const DevJoin& J0 = a.q.joins[0];
   const bool fixed = preload && a.q.acc_mode == kAccSingle && a.q.n_joins == 1 &&
                      (a.q.n_preds == 1 || a.q.n_preds == 2) && J0.card <= 0 && J0.hash.steps == 0u &&
-                     J0.hash.mult == 1u && J0.hash.shift == 0u && J0.hash.mask == 0xFFFFFFFFu &&
+                     J0.hash.mult_hi == 1u && J0.hash.mult_lo == 0u && J0.hash.shift == 0u && J0.hash.mask == 0xFFFFFFFFu &&
                      (a.q.agg_op == CRYS_AGG_A_MUL_B || a.q.agg_op == CRYS_AGG_A);
   if (fixed) {
     const bool mul = a.q.agg_op == CRYS_AGG_A_MUL_B;
@@ -1903,7 +1903,7 @@ void assign_probes(ScanArgs& a) {
   int n = 0;
   auto same = [](const ProbeSpec& p, const DevJoin& J) {
     return p.slots == J.slots && p.fk_col == J.fk_col && p.hash.mask == J.hash.mask && p.hash.limit == J.hash.limit &&
-           p.hash.mult == J.hash.mult;
+           p.hash.mult_hi == J.hash.mult_hi && p.hash.mult_lo == J.hash.mult_lo;
   };
   for (int qi = 0; qi < a.n_queries; ++qi) {
     for (int j = 0; j < a.q[qi].n_joins; ++j) {
