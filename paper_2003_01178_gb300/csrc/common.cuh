@@ -177,8 +177,12 @@ __device__ __forceinline__ void st_relaxed_u32(uint32_t* p, uint32_t v) {
 // With the 32-bit constant 2654435769 (2^32/phi) instead, dense keys 0..n-1 cluster at
 // some sizes: a lookup examines 2.3 slots on average at n = 2^22 (1.7 at 2^21, 1.3 at
 // 2^20) against 1.0 with the 64-bit product at every n from 2^10 to 2^27; random keys
-// examine the 1.5 of linear probing at 50% fill either way.  Identity hashing (key mod
-// capacity) uses mult = 2^32 (mult_hi = 1, mult_lo = 0), shift = 0.
+// examine the 1.5 of linear probing at 50% fill either way.  Tables of at most
+// kSmallHashSlots slots keep the 32-bit constant (mult_lo = 0: their dense keys do not
+// cluster, 1.003 slots at most), so that a probe of a table held in shared memory needs
+// one multiply.  Identity hashing (key mod capacity) uses mult = 2^32 (mult_hi = 1,
+// mult_lo = 0), shift = 0.
+constexpr int64_t kSmallHashSlots = 4096;
 struct HashFn {
   uint32_t mult_hi, mult_lo;
   uint32_t shift, mask;
@@ -208,6 +212,10 @@ __host__ __device__ __forceinline__ HashFn make_hash(int32_t kind, int64_t capac
     h.mult_hi = 1u;
     h.mult_lo = 0u;
     h.shift = 0u;
+  } else if (capacity <= kSmallHashSlots) {
+    h.mult_hi = 2654435769u;
+    h.mult_lo = 0u;
+    h.shift = 32u - log2cap;
   } else {
     h.mult_hi = 0x9E3779B9u;
     h.mult_lo = 0x7F4A7C15u;
@@ -219,6 +227,10 @@ __host__ __device__ __forceinline__ HashFn make_hash(int32_t kind, int64_t capac
 __device__ __forceinline__ uint32_t hash_slot(int32_t key, const HashFn& f) {
   const uint32_t k = static_cast<uint32_t>(key);
   return ((k * f.mult_hi + __umulhi(k, f.mult_lo)) >> f.shift) & f.mask;
+}
+// The same for a table of at most kSmallHashSlots slots (mult_lo is 0 for every kind).
+__device__ __forceinline__ uint32_t hash_slot_small(int32_t key, const HashFn& f) {
+  return ((static_cast<uint32_t>(key) * f.mult_hi) >> f.shift) & f.mask;
 }
 
 // Whether a key can be in the table at all (direct tables: 0 <= key < capacity).

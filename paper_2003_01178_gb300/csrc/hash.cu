@@ -88,6 +88,7 @@ struct ProbeArgs {
 // A table of at most this many bytes is copied into every block's shared memory: random
 // slot reads then cost shared-memory wavefronts instead of L1 tag lookups.
 constexpr int64_t kSmemTableBytes = 32 * 1024;
+static_assert(kSmemTableBytes / 8 <= kSmallHashSlots, "a table in shared memory hashes with one multiply");
 
 template <int THREADS, int ITEMS, bool SMEM_TABLE>
 __global__ void __launch_bounds__(THREADS) probe_kernel(ProbeArgs a) {
@@ -185,7 +186,7 @@ __global__ void __launch_bounds__(THREADS) probe_kernel(ProbeArgs a) {
     uint64_t slot[ITEMS];
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
-      h[i] = hash_slot(key[i], a.hash);
+      h[i] = SMEM_TABLE ? hash_slot_small(key[i], a.hash) : hash_slot(key[i], a.hash);
       const bool look = ((live >> i) & 1u) && hash_may_hold(key[i], a.hash);
       if (SMEM_TABLE)
         slot[i] = look ? tbl[h[i]] : kEmptySlot;
