@@ -140,7 +140,8 @@ int crys_project(const float* x1, const float* x2, int64_t n, float a, float b, 
  * at 50% fill, i.e. capacity = 2 * rows.  Home slot of key k:
  *   CRYS_HASH_MULT   (0, default) multiplicative (Fibonacci) hashing, the top
  *                    log2(capacity) bits of the 64-bit product
- *                    (uint64)(uint32)k * 0x9E3779B97F4A7C15;
+ *                    (uint64)(uint32)k * 0x9E3779B97F4A7C15; for a capacity of at most
+ *                    4096 slots, (uint32)(k * 2654435769) >> (32 - log2(capacity));
  *   CRYS_HASH_IDENT  (1) k mod capacity: perfect hashing when the keys are dense
  *                    (0..n-1 with capacity >= n, as for star-schema dimension keys; the
  *                    paper's Section 5.3 cost model assumes perfect hashing), so a table
